@@ -1,0 +1,184 @@
+/*
+ * kohler.h — C ABI of libkohler, a CUDA (sm_103a) implementation of Köhler's
+ * boundary-contrast curve and its thresholds, after "Speeding up the Köhler's
+ * method of contrast thresholding" (G. Noyel).
+ *
+ * Definitions (Section 2.1).  An image f has W x H pixels with integer values in
+ * [0, M[.  For a threshold t in [0, M[:
+ *   B(t)    = { (x0, x1) : x1 a 4-neighbour of x0, f(x0) <= t < f(x1) }       (Eq. 1)
+ *   card(t) = #B(t)
+ *   sumc(t) = sum over B(t) of min(f(x1) - t, t - f(x0))                        (Eq. 2)
+ *   C(t)    = sumc(t) / card(t)  (mean boundary contrast, Eq. 3); 0 when card(t) = 0
+ *   t0      = first t with the largest C(t)                                      (Eq. 4)
+ * The thresholds of a multi-level split are the local maxima of C (text after
+ * Eq. 4).  Only pairs with both pixels inside the image exist.  Section 3.2
+ * (Eq. 7-9) shows that scanning each unordered neighbour pair once (right and
+ * lower neighbour, the half neighbourhood N4*) gives the same card and sumc.
+ *
+ * Exactness: card and sumc are exact unsigned 64-bit integers.  C(t) is the
+ * IEEE-754 double quotient, rounded to nearest, of the two integers converted to
+ * double.  Thresholds compare C values exactly (cross products in 128 bits), so
+ * two thresholds with equal quotients tie even when their doubles would not.
+ *
+ * Conventions shared by every entry point:
+ *  - Pixels: row-major, `pitch_bytes` between row starts, KOHLER_U8 (1 byte) or
+ *    KOHLER_U16 (2 bytes, little-endian).  width >= 1, height >= 1,
+ *    pitch_bytes >= width * bytes-per-pixel.
+ *  - M: 2 <= M <= 256 for KOHLER_U8, 2 <= M <= 65536 for KOHLER_U16.
+ *  - Device pointers are CUDA global-memory addresses of the current device;
+ *    `cuda_stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *    that take a stream only enqueue work and return; results are valid once
+ *    the stream has reached that point.
+ *  - The caller owns every buffer it passes; the library never frees them.
+ *    The library keeps an internal device workspace per (device, stream), made
+ *    on first use (cudaMalloc) and freed at unload or by kohler_release().  Do
+ *    a first call on a stream before capturing that stream into a CUDA graph.
+ *  - Reads of an image may touch bytes after the last pixel of a row up to the
+ *    next multiple of 8 bytes; those bytes never change a result.
+ *  - Every call returns a kohler_status; none aborts.  A pixel value >= M is
+ *    found on the device: that image's outputs are all zero and the next
+ *    kohler_stream_status() on the stream returns KOHLER_ERR_RANGE.
+ */
+#ifndef KOHLER_H
+#define KOHLER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { KOHLER_U8 = 1, KOHLER_U16 = 2 } kohler_dtype;
+
+/* Neighbourhood of the boundary pairs (Section 2: N4; 8- and 6-neighbourhoods
+ * are mentioned as alternatives but not defined further).  Only N4. */
+typedef enum { KOHLER_N4 = 4 } kohler_nbhd;
+
+typedef enum {
+  KOHLER_OK = 0,
+  KOHLER_PENDING = 1,          /* kohler_poll: result not ready yet */
+  KOHLER_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, ...) */
+  KOHLER_ERR_UNSUPPORTED = -2, /* valid but not implemented (e.g. other neighbourhood) */
+  KOHLER_ERR_RANGE = -3,       /* a pixel value was >= M */
+  KOHLER_ERR_NOMEM = -4,       /* device or pinned host allocation failed */
+  KOHLER_ERR_CUDA = -5,        /* a CUDA runtime call failed */
+  KOHLER_ERR_TIMEOUT = -6,     /* kohler_poll: timeout elapsed */
+  KOHLER_ERR_BUSY = -7         /* kohler_submit: staging queue full */
+} kohler_status;
+
+/* One image in device memory (for the batched call). */
+typedef struct {
+  const void* img;     /* device pointer to pixel (0, 0) */
+  int64_t width;       /* pixels per row */
+  int64_t height;      /* rows */
+  int64_t pitch_bytes; /* bytes between row starts */
+} kohler_image;
+
+/* Contrast curve of one device image (Eq. 1-3 for every t in [0, M[).
+ * card, sumc: device uint64[M]; curve: device double[M] (may be NULL).
+ * Work: one streaming pass over the image's N4* pairs into integer histograms,
+ * then an M-bin scan that yields card and sumc exactly. */
+int kohler_curve(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
+                 int32_t M, kohler_nbhd nb, uint64_t* card, uint64_t* sumc, double* curve,
+                 void* cuda_stream);
+
+/* Contrast curves of n images with one dtype and M, in one launch (or one per
+ * 64 images).  imgs: HOST array of n descriptors (read before the call returns).
+ * card, sumc: device uint64[n][M]; curve: device double[n][M] (may be NULL). */
+int kohler_curve_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
+                       uint64_t* card, uint64_t* sumc, double* curve, void* cuda_stream);
+
+/* Thresholds from n exact curves (device card/sumc, [n][M]): the local maxima of C
+ * (a plateau of equal C among thresholds with card > 0 is one maximum when both
+ * outside neighbours are absent or strictly lower, reported by its first t),
+ * ranked by C descending then t ascending (Section 2.1, Eq. 4 and after).
+ * out_t: device int32[n][max_k] (the first min(count, max_k) ranked maxima, then -1;
+ * may be NULL when max_k = 0); out_count: device int32[n] (total local maxima);
+ * out_t0: device int32[n] (t0 of Eq. 4, -1 if every card(t) is 0). */
+int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int32_t M, int32_t max_k,
+                      int32_t* out_t, int32_t* out_count, int32_t* out_t0, void* cuda_stream);
+
+/* kohler_curve_batch followed by kohler_thresholds, fused: the last block to
+ * finish an image computes its curve and thresholds in the same launch.
+ * Outputs as in the two calls above (curve may be NULL). */
+int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
+                         int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
+                         int32_t* out_count, int32_t* out_t0, void* cuda_stream);
+
+/* Whole path from HOST memory and back, synchronously: the image is copied to the
+ * device in row bands on a copy stream while earlier bands are already being
+ * reduced, then card/sumc/curve and the thresholds are copied back.
+ * img: host pointer (pinned memory gives the fastest copies); outputs: HOST
+ * arrays card/sumc uint64[M], curve double[M], out_t int32[max_k] (any output
+ * may be NULL).  Returns KOHLER_ERR_RANGE directly for a pixel >= M. */
+int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
+                        int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc,
+                        double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0);
+
+/* Waits for `cuda_stream` and returns the deferred status of the calls enqueued
+ * on it since the previous kohler_stream_status: KOHLER_ERR_RANGE if an image had
+ * a pixel >= M, KOHLER_ERR_CUDA on a CUDA error, else KOHLER_OK. */
+int kohler_stream_status(void* cuda_stream);
+
+/* Frees the workspaces of the current device (all streams).  Only call when no
+ * work of this library is in flight on the device. */
+int kohler_release(void);
+
+/* Static text for a status code. */
+const char* kohler_strerror(int status);
+
+/* ---------------------------------------------------------------- serving
+ * A server turns a stream of host frames into curves and thresholds with
+ * continuous batching (the video use of Section 4, Table 2): a host thread
+ * admits submitted frames into device slots as slots and device memory free
+ * up, copies them on a copy stream, and each launch reduces every frame that
+ * is resident and copied at that moment; results are copied back per frame.
+ * Frames are uint8 or uint16 with the server's M. */
+typedef struct kohler_server kohler_server;
+
+typedef struct {
+  int32_t t0;          /* Eq. 4 optimal threshold, -1 if none */
+  int32_t count;       /* total number of local maxima */
+  int32_t* thresholds; /* caller buffer of max_k entries (ranked maxima, -1 padded), or NULL */
+  double latency_s;    /* submit -> result available on the host, seconds */
+  int64_t width, height;
+} kohler_result;
+
+/* device_mem_budget: bytes of device memory the server may hold for frame
+ * buffers (0 = 1 GiB); a frame larger than the budget finishes with
+ * KOHLER_ERR_NOMEM.  max_inflight: output slots (0 = 64); a frame holds one from
+ * admission until its ticket is polled, so at most max_inflight frames are
+ * admitted or finished-but-unpolled at once.  max_k: thresholds kept per frame.
+ * Pinned staging for submitted frames is capped at 1 GiB. */
+int kohler_server_create(kohler_server** s, int32_t M, int32_t max_k, size_t device_mem_budget,
+                         int32_t max_inflight);
+
+/* Copies the frame (row-major, pitch_bytes) into pinned staging and queues it;
+ * the caller may reuse `host_frame` as soon as the call returns.  *ticket
+ * identifies the frame.  KOHLER_ERR_BUSY when the staging queue is full. */
+int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                  int64_t pitch_bytes, uint64_t* ticket);
+
+/* Result of a ticket: KOHLER_OK (out filled, ticket released), KOHLER_PENDING when
+ * timeout_us = 0 and not ready, KOHLER_ERR_TIMEOUT after timeout_us microseconds
+ * (timeout_us < 0 waits without limit), KOHLER_ERR_RANGE for a frame with a pixel
+ * >= M, KOHLER_ERR_ARG for an unknown ticket. */
+int kohler_poll(kohler_server* s, uint64_t ticket, kohler_result* out, int64_t timeout_us);
+
+/* Device copy of a finished frame's curve (double[M]) valid until the ticket is
+ * polled; NULL pointer if the ticket is unknown or not finished. */
+int kohler_server_curve(kohler_server* s, uint64_t ticket, const double** dev_curve);
+
+/* Counters: frames submitted, finished, launches made, frames per launch (max). */
+int kohler_server_stats(kohler_server* s, uint64_t* submitted, uint64_t* finished, uint64_t* launches,
+                        uint64_t* max_frames_per_launch);
+
+/* Drains in-flight frames, stops the server thread and frees everything. */
+int kohler_server_destroy(kohler_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KOHLER_H */

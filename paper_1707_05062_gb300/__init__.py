@@ -1,0 +1,217 @@
+"""Python binding of libkohler: Köhler's boundary-contrast curve and thresholds on GB300.
+
+A thin ctypes layer over the C ABI declared in ``include/kohler.h``: it only
+marshals arguments.  Every step of the computation runs in the library's CUDA
+kernels; PyTorch provides device memory and streams.  There is no CPU fallback:
+if ``libkohler.so`` has not been built, every call raises.
+
+Images are 2-D tensors (row-major, unit stride along a row) of dtype
+``torch.uint8`` or 16-bit (``torch.uint16`` or ``torch.int16``, read as unsigned).
+Curves come back as int64 tensors holding the exact uint64 counts (all values
+here stay below 2^63) and a float64 curve.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkohler.so")
+
+KOHLER_U8, KOHLER_U16 = 1, 2
+KOHLER_N4 = 4
+OK, PENDING = 0, 1
+ERR_ARG, ERR_UNSUPPORTED, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY = -1, -2, -3, -4, -5, -6, -7
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KohlerError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = lib().kohler_strerror(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})" if what else f"{msg} ({status})")
+
+
+class KohlerImage(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("width", ctypes.c_int64), ("height", ctypes.c_int64),
+                ("pitch_bytes", ctypes.c_int64)]
+
+
+class KohlerResult(ctypes.Structure):
+    _fields_ = [("t0", ctypes.c_int32), ("count", ctypes.c_int32), ("thresholds", ctypes.c_void_p),
+                ("latency_s", ctypes.c_double), ("width", ctypes.c_int64), ("height", ctypes.c_int64)]
+
+
+def lib():
+    """The loaded libkohler (raises if it is missing: no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libkohler.so is not built ({LIB_PATH}); run paper_1707_05062_gb300.build.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            p, i32, i64, i = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+            L.kohler_curve.argtypes = [p, i, i64, i64, i64, i32, i, p, p, p, p]
+            L.kohler_curve_batch.argtypes = [p, i32, i, i32, i, p, p, p, p]
+            L.kohler_thresholds.argtypes = [p, p, i32, i32, i32, p, p, p, p]
+            L.kohler_analyze_batch.argtypes = [p, i32, i, i32, i, i32, p, p, p, p, p, p, p]
+            L.kohler_analyze_host.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p]
+            L.kohler_stream_status.argtypes = [p]
+            L.kohler_release.argtypes = []
+            L.kohler_strerror.argtypes = [i]
+            L.kohler_strerror.restype = ctypes.c_char_p
+            for name in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_analyze_batch",
+                         "kohler_analyze_host", "kohler_stream_status", "kohler_release"):
+                getattr(L, name).restype = i
+            if hasattr(L, "kohler_server_create"):
+                L.kohler_server_create.argtypes = [p, i32, i32, ctypes.c_size_t, i32]
+                L.kohler_submit.argtypes = [p, p, i, i64, i64, i64, p]
+                L.kohler_poll.argtypes = [p, ctypes.c_uint64, p, i64]
+                L.kohler_server_curve.argtypes = [p, ctypes.c_uint64, p]
+                L.kohler_server_stats.argtypes = [p, p, p, p, p]
+                L.kohler_server_destroy.argtypes = [p]
+                for name in ("kohler_server_create", "kohler_submit", "kohler_poll", "kohler_server_curve",
+                             "kohler_server_stats", "kohler_server_destroy"):
+                    getattr(L, name).restype = i
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise KohlerError(rc, what)
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.uint8:
+        return KOHLER_U8
+    if t.dtype in (torch.int16, getattr(torch, "uint16", torch.int16)):
+        return KOHLER_U16
+    raise TypeError(f"image dtype must be uint8 or 16-bit, got {t.dtype}")
+
+
+def _image(t: torch.Tensor):
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("image must be a 2-D tensor with unit stride along rows")
+    return t.data_ptr(), t.shape[1], t.shape[0], t.stride(0) * t.element_size()
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream if hasattr(s, "cuda_stream") else int(s)
+
+
+def _images(imgs: Sequence[torch.Tensor]):
+    arr = (KohlerImage * max(1, len(imgs)))()
+    codes = set()
+    for k, t in enumerate(imgs):
+        if not t.is_cuda:
+            raise ValueError("images must be on the GPU")
+        ptr, w, h, pitch = _image(t)
+        arr[k] = KohlerImage(ptr, w, h, pitch)
+        codes.add(_dtype_code(t))
+    if len(codes) > 1:
+        raise ValueError("all images of a batch must have one dtype")
+    return arr, (codes.pop() if codes else KOHLER_U8)
+
+
+def curve(img: torch.Tensor, M: int, *, with_curve: bool = True, stream=None):
+    """(card, sumc, curve) of one device image: int64[M], int64[M], float64[M] (or None)."""
+    dev = img.device
+    card = torch.empty(M, dtype=torch.int64, device=dev)
+    sumc = torch.empty(M, dtype=torch.int64, device=dev)
+    c = torch.empty(M, dtype=torch.float64, device=dev) if with_curve else None
+    ptr, w, h, pitch = _image(img)
+    _check(lib().kohler_curve(ptr, _dtype_code(img), w, h, pitch, M, KOHLER_N4, card.data_ptr(), sumc.data_ptr(),
+                              c.data_ptr() if c is not None else None, _stream(stream)), "kohler_curve")
+    return card, sumc, c
+
+
+def curve_batch(imgs: Sequence[torch.Tensor], M: int, *, with_curve: bool = True, stream=None):
+    """(card, sumc, curve) of n device images: [n, M] each (curve may be None)."""
+    n = len(imgs)
+    dev = imgs[0].device if n else torch.device("cuda")
+    arr, code = _images(imgs)
+    card = torch.empty((n, M), dtype=torch.int64, device=dev)
+    sumc = torch.empty((n, M), dtype=torch.int64, device=dev)
+    c = torch.empty((n, M), dtype=torch.float64, device=dev) if with_curve else None
+    _check(lib().kohler_curve_batch(arr, n, code, M, KOHLER_N4, card.data_ptr(), sumc.data_ptr(),
+                                    c.data_ptr() if c is not None else None, _stream(stream)), "kohler_curve_batch")
+    return card, sumc, c
+
+
+def thresholds(card: torch.Tensor, sumc: torch.Tensor, max_k: int, *, stream=None):
+    """(ranked maxima int32[n, max_k], count int32[n], t0 int32[n]) from exact curves."""
+    if card.dim() == 1:
+        card, sumc = card[None], sumc[None]
+    card, sumc = card.contiguous(), sumc.contiguous()
+    n, M = card.shape
+    dev = card.device
+    out_t = torch.empty((n, max(max_k, 1)), dtype=torch.int32, device=dev)
+    cnt = torch.empty(n, dtype=torch.int32, device=dev)
+    t0 = torch.empty(n, dtype=torch.int32, device=dev)
+    _check(lib().kohler_thresholds(card.data_ptr(), sumc.data_ptr(), n, M, max_k, out_t.data_ptr(), cnt.data_ptr(),
+                                   t0.data_ptr(), _stream(stream)), "kohler_thresholds")
+    return out_t[:, :max_k], cnt, t0
+
+
+def analyze_batch(imgs: Sequence[torch.Tensor], M: int, max_k: int, *, with_curve: bool = True, stream=None,
+                  out=None):
+    """Fused curves and thresholds of n device images (one launch per 64 images).
+    Returns (card, sumc, curve, out_t, count, t0); `out` may supply these tensors."""
+    n = len(imgs)
+    dev = imgs[0].device
+    arr, code = _images(imgs)
+    if out is None:
+        out = (torch.empty((n, M), dtype=torch.int64, device=dev), torch.empty((n, M), dtype=torch.int64, device=dev),
+               torch.empty((n, M), dtype=torch.float64, device=dev) if with_curve else None,
+               torch.empty((n, max(max_k, 1)), dtype=torch.int32, device=dev),
+               torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
+    card, sumc, c, out_t, cnt, t0 = out
+    _check(lib().kohler_analyze_batch(arr, n, code, M, KOHLER_N4, max_k, card.data_ptr(), sumc.data_ptr(),
+                                      c.data_ptr() if c is not None else None, out_t.data_ptr(), cnt.data_ptr(),
+                                      t0.data_ptr(), _stream(stream)), "kohler_analyze_batch")
+    return card, sumc, c, out_t[:, :max_k], cnt, t0
+
+
+def analyze_host(img, M: int, max_k: int):
+    """Whole path from a host image (numpy array or CPU tensor, pinned is fastest) back
+    to host results: (card, sumc, curve, thresholds, count, t0) as numpy arrays."""
+    import numpy as np
+
+    if isinstance(img, torch.Tensor):
+        if img.is_cuda:
+            raise ValueError("analyze_host takes a host image")
+        code = _dtype_code(img)
+        ptr, w, h, pitch = _image(img)
+    else:
+        a = np.asarray(img)
+        if a.dtype not in (np.uint8, np.uint16) or a.ndim != 2 or a.strides[1] != a.itemsize:
+            raise ValueError("host image must be a 2-D uint8/uint16 array with unit stride along rows")
+        code = KOHLER_U8 if a.dtype == np.uint8 else KOHLER_U16
+        ptr, w, h, pitch = a.ctypes.data, a.shape[1], a.shape[0], a.strides[0]
+    card = np.empty(M, np.uint64)
+    sumc = np.empty(M, np.uint64)
+    c = np.empty(M, np.float64)
+    ts = np.empty(max(max_k, 1), np.int32)
+    cnt = np.zeros(1, np.int32)
+    t0 = np.zeros(1, np.int32)
+    _check(lib().kohler_analyze_host(ptr, code, w, h, pitch, M, KOHLER_N4, max_k, card.ctypes.data,
+                                     sumc.ctypes.data, c.ctypes.data, ts.ctypes.data, cnt.ctypes.data,
+                                     t0.ctypes.data), "kohler_analyze_host")
+    return card, sumc, c, ts[:max_k], int(cnt[0]), int(t0[0])
+
+
+def stream_status(stream=None) -> int:
+    """Deferred status of the calls on a stream (waits for it): OK or ERR_RANGE/ERR_CUDA."""
+    return lib().kohler_stream_status(_stream(stream))
+
+
+def release() -> None:
+    _check(lib().kohler_release(), "kohler_release")

@@ -1,0 +1,551 @@
+// libkohler C ABI: argument checks, per-stream device workspace, choice of the
+// pass for each image and launch of the fused pass + epilogue kernels.
+#include "kohler.h"
+#include "kohler_device.cuh"
+#include "kohler_internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+using namespace kohler;
+
+namespace {
+
+constexpr int kFastWarps = 8;
+constexpr int kGenericWarps = 8;
+constexpr int kRowsPerWarp = 16;     // target rows per warp when sizing the grid
+constexpr int kMaxSmemBins = 4096;   // largest M reduced in shared memory
+
+struct Workspace {
+  int device = -1;
+  cudaStream_t stream = nullptr;
+  void* mem = nullptr;
+  int slots = 0, bins = 0, cand_stride = 0;
+  unsigned long long* hist = nullptr;
+  unsigned int* done = nullptr;
+  unsigned int* err = nullptr;
+  unsigned int* sticky = nullptr;
+  int32_t* cand = nullptr;
+};
+
+std::mutex g_mu;
+std::map<std::pair<int, uintptr_t>, Workspace*> g_ws;
+
+int status_of(cudaError_t e) {
+  if (e == cudaSuccess) return KOHLER_OK;
+  if (e == cudaErrorMemoryAllocation) return KOHLER_ERR_NOMEM;
+  return KOHLER_ERR_CUDA;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace of (current device, stream) with at least `slots` slots of `bins` bins.
+// Newly allocated memory is zeroed on the stream; a replaced workspace is freed
+// after the stream has drained.
+int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Workspace** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto key = std::make_pair(dev, (uintptr_t)stream);
+  Workspace*& w = g_ws[key];
+  if (!w) {
+    w = new Workspace();
+    w->device = dev;
+    w->stream = stream;
+  }
+  if (w->mem && w->slots >= slots && w->bins >= bins && w->cand_stride >= cand_stride) {
+    *out = w;
+    return KOHLER_OK;
+  }
+  slots = std::max(slots, w->slots);
+  bins = std::max(bins, w->bins);
+  cand_stride = std::max(cand_stride, w->cand_stride);
+  if (w->mem) {
+    e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return status_of(e);
+    cudaFree(w->mem);
+    w->mem = nullptr;
+  }
+  const size_t hist_b = align256((size_t)slots * 4 * bins * sizeof(unsigned long long));
+  const size_t done_b = align256((size_t)slots * sizeof(unsigned));
+  const size_t err_b = align256((size_t)slots * sizeof(unsigned));
+  const size_t sticky_b = 256;
+  const size_t cand_b = align256((size_t)slots * cand_stride * sizeof(int32_t));
+  const size_t total = hist_b + done_b + err_b + sticky_b + cand_b;
+  void* mem = nullptr;
+  e = cudaMalloc(&mem, total);
+  if (e != cudaSuccess) {
+    w->slots = w->bins = w->cand_stride = 0;
+    return status_of(e);
+  }
+  e = cudaMemsetAsync(mem, 0, hist_b + done_b + err_b + sticky_b, stream);
+  if (e != cudaSuccess) {
+    cudaFree(mem);
+    return status_of(e);
+  }
+  char* p = static_cast<char*>(mem);
+  w->mem = mem;
+  w->hist = reinterpret_cast<unsigned long long*>(p);
+  w->done = reinterpret_cast<unsigned*>(p + hist_b);
+  w->err = reinterpret_cast<unsigned*>(p + hist_b + done_b);
+  w->sticky = reinterpret_cast<unsigned*>(p + hist_b + done_b + err_b);
+  w->cand = reinterpret_cast<int32_t*>(p + hist_b + done_b + err_b + sticky_b);
+  w->slots = slots;
+  w->bins = bins;
+  w->cand_stride = cand_stride;
+  *out = w;
+  return KOHLER_OK;
+}
+
+enum class Pass { FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16 };
+
+int bins_for(kohler_dtype dt, int M) { return dt == KOHLER_U8 ? 256 : ((M + 31) / 32) * 32; }
+
+int check_image(const void* img, kohler_dtype dt, int64_t W, int64_t H, int64_t pitch) {
+  if (!img || W < 1 || H < 1) return KOHLER_ERR_ARG;
+  if (W > (int64_t)1 << 30 || H > (int64_t)1 << 30) return KOHLER_ERR_ARG;
+  const int es = dt == KOHLER_U8 ? 1 : 2;
+  if (pitch < W * es) return KOHLER_ERR_ARG;
+  if (dt == KOHLER_U16 && (((uintptr_t)img & 1) || (pitch & 1))) return KOHLER_ERR_ARG;
+  // the done counter of an image is 32-bit: strips x rows of the narrowest strip width
+  if (((W + 31) / 32) * H >= ((int64_t)1 << 32)) return KOHLER_ERR_ARG;
+  return KOHLER_OK;
+}
+
+int check_common(kohler_dtype dt, int32_t M, kohler_nbhd nb) {
+  if (dt != KOHLER_U8 && dt != KOHLER_U16) return KOHLER_ERR_ARG;
+  if (M < 2 || (dt == KOHLER_U8 && M > 256) || (dt == KOHLER_U16 && M > 65536)) return KOHLER_ERR_ARG;
+  if (nb != KOHLER_N4) return KOHLER_ERR_UNSUPPORTED;
+  return KOHLER_OK;
+}
+
+Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
+  const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
+  if (dt == KOHLER_U8) {
+    if (aligned8 && im.width % 8 == 0) return M == 256 ? Pass::FastU8 : Pass::FastU8Check;
+    return Pass::GenericU8;
+  }
+  if (M > kMaxSmemBins) return Pass::GlobalU16;
+  if (aligned8 && im.width % 4 == 0) return Pass::FastU16;
+  return Pass::GenericU16;
+}
+
+int strip_px(Pass p) {
+  switch (p) {
+    case Pass::FastU8:
+    case Pass::FastU8Check: return 256;
+    case Pass::FastU16: return 32 * TraitsU16::PX;
+    default: return 32;
+  }
+}
+
+struct KernelInfo {
+  const void* fn;
+  int threads;
+  size_t smem;
+};
+
+KernelInfo kernel_for(Pass p, int bins) {
+  switch (p) {
+    case Pass::FastU8:
+      return {(const void*)k_u8<kFastWarps, false>, kFastWarps * 32, (size_t)(u8::kWords + kFastWarps * 256) * 4};
+    case Pass::FastU8Check:
+      return {(const void*)k_u8<kFastWarps, true>, kFastWarps * 32, (size_t)(u8::kWords + kFastWarps * 256) * 4};
+    case Pass::FastU16:
+      return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
+    case Pass::GenericU8: return {(const void*)k_generic<1, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16: return {(const void*)k_generic<2, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU8: return {(const void*)k_generic<1, true>, kGenericWarps * 32, 0};
+    case Pass::GlobalU16: return {(const void*)k_generic<2, true>, kGenericWarps * 32, 0};
+  }
+  return {nullptr, 0, 0};
+}
+
+// Shared memory the last block of an image can use to stage the epilogue: the
+// curves and threshold candidates, plus the histograms when the whole set fits
+// below 100 KB (the block's own pass needs `pass_smem`).
+size_t epilogue_smem(int M, int bins, size_t pass_smem) {
+  const size_t cs = (size_t)2 * M * 8 + (((size_t)(M + 1) / 2 + 2) * 4 + 15) / 16 * 16;
+  const size_t full = cs + (size_t)4 * bins * 8;
+  const size_t cap = 100 * 1024;
+  if (full <= cap) return full;
+  if (cs <= cap || cs <= pass_smem) return cs;
+  return 0;
+}
+
+// Grid size: enough blocks for ~kRowsPerWarp rows per warp, at most one full
+// wave of resident blocks.
+int grid_for(const KernelInfo& k, int64_t total_rs) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (k.smem > 48 * 1024) cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int64_t warps = k.threads / 32;
+  int64_t want = (total_rs + warps * kRowsPerWarp - 1) / (warps * kRowsPerWarp);
+  want = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+  return (int)want;
+}
+
+struct Band {
+  int32_t y0, y1;
+};
+
+// Launches the pass over `count` images (all of one Pass) already described in
+// `idx` (indices into imgs); slots = position in the launch.
+int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* imgs, const std::vector<Band>* bands,
+                 int M, int bins, Workspace* ws, LaunchParams& base, cudaStream_t stream, const std::vector<int>& slot_of,
+                 const int* out_index) {
+  if (idx.empty()) return KOHLER_OK;
+  const int spx = strip_px(pass);
+  LaunchParams P = base;
+  P.n = 0;
+  int64_t rs = 0;
+  for (size_t j = 0; j < idx.size(); ++j) {
+    const int i = idx[j];
+    const kohler_image& im = imgs[i];
+    ImgDesc& d = P.img[P.n];
+    d.base = static_cast<const unsigned char*>(im.img);
+    d.pitch = im.pitch_bytes;
+    d.W = (int32_t)im.width;
+    d.H = (int32_t)im.height;
+    d.y0 = bands ? (*bands)[i].y0 : 0;
+    d.y1 = bands ? (*bands)[i].y1 : (int32_t)im.height;
+    if (d.y1 <= d.y0) continue;
+    d.strips = (int32_t)((im.width + spx - 1) / spx);
+    d.slot = slot_of[i];
+    d.out = out_index ? out_index[i] : i;
+    d.rs_begin = rs;
+    d.pad_ = 0;
+    rs += (int64_t)d.strips * (d.y1 - d.y0);
+    ++P.n;
+  }
+  if (P.n == 0) return KOHLER_OK;
+  P.total_rs = rs;
+  P.bins = bins;
+  P.M = M;
+  KernelInfo k = kernel_for(pass, bins);
+  k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
+  P.smem_bytes = (int32_t)k.smem;
+  const int grid = grid_for(k, rs);
+  void* args[] = {&P};
+  cudaError_t e = cudaLaunchKernel(k.fn, dim3(grid), dim3(k.threads), args, k.smem, stream);
+  return status_of(e);
+}
+
+// Shared driver of kohler_curve_batch / kohler_analyze_batch / banded host path.
+// `base_out` offsets output indices (images imgs[i] write row base_out + i).
+int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, int32_t max_k, uint64_t* card,
+              uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0,
+              cudaStream_t stream, const std::vector<Band>* bands, const int* out_index = nullptr,
+              int32_t* out_status = nullptr) {
+  const int bins = bins_for(dt, M);
+  const int cand_stride = (M + 1) / 2 + 2;
+  const int chunk = std::min<int>(kMaxBatch, std::max<int>(1, (int)std::min<int64_t>(
+                                                               kMaxBatch, ((int64_t)256 << 20) / ((int64_t)bins * 32))));
+  Workspace* ws = nullptr;
+  int rc = get_workspace(stream, chunk, bins, cand_stride, &ws);
+  if (rc) return rc;
+  for (int c0 = 0; c0 < n; c0 += chunk) {
+    const int cn = std::min(chunk, n - c0);
+    LaunchParams base;
+    memset(&base, 0, sizeof(base));
+    base.M = M;
+    base.max_k = max_k;
+    // with explicit output indices the output arrays are addressed directly
+    const size_t o0 = out_index ? 0 : (size_t)c0;
+    base.card = card + o0 * M;
+    base.sumc = sumc + o0 * M;
+    base.curve = curve ? curve + o0 * M : nullptr;
+    base.out_t = (out_t && max_k > 0) ? out_t + o0 * max_k : nullptr;
+    base.out_count = out_count ? out_count + o0 : nullptr;
+    base.out_t0 = out_t0 ? out_t0 + o0 : nullptr;
+    base.out_status = out_status ? out_status + o0 : nullptr;
+    base.hist = ws->hist;
+    base.done = ws->done;
+    base.err = ws->err;
+    base.sticky = ws->sticky;
+    base.cand = ws->cand;
+    base.cand_stride = ws->cand_stride;
+    std::map<Pass, std::vector<int>> groups;
+    std::vector<int> slot_of(cn);
+    for (int j = 0; j < cn; ++j) {
+      groups[pass_for(imgs[c0 + j], dt, M)].push_back(j);
+      slot_of[j] = j;
+    }
+    std::vector<Band> sub_bands;
+    if (bands) sub_bands.assign(bands->begin() + c0, bands->begin() + c0 + cn);
+    for (auto& g : groups) {
+      rc = launch_group(g.first, g.second, imgs + c0, bands ? &sub_bands : nullptr, M, bins, ws, base, stream, slot_of,
+                        out_index ? out_index + c0 : nullptr);
+      if (rc) return rc;
+    }
+  }
+  return KOHLER_OK;
+}
+
+int validate_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb) {
+  int rc = check_common(dt, M, nb);
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && !imgs)) return KOHLER_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    rc = check_image(imgs[i].img, dt, imgs[i].width, imgs[i].height, imgs[i].pitch_bytes);
+    if (rc) return rc;
+  }
+  return KOHLER_OK;
+}
+
+}  // namespace
+
+namespace kohler {
+int launch_images(const kohler_image* imgs, int n, kohler_dtype dt, int M, const int* out_index, const OutSpec& o,
+                  cudaStream_t stream) {
+  int rc = validate_batch(imgs, n, dt, M, KOHLER_N4);
+  if (rc) return rc;
+  if (n == 0) return KOHLER_OK;
+  return run_batch(imgs, n, dt, M, o.max_k, o.card, o.sumc, o.curve, o.out_t, o.out_count, o.out_t0, stream, nullptr,
+                   out_index, o.out_status);
+}
+}  // namespace kohler
+
+extern "C" {
+
+int kohler_curve(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes, int32_t M,
+                 kohler_nbhd nb, uint64_t* card, uint64_t* sumc, double* curve, void* cuda_stream) {
+  kohler_image im{img, width, height, pitch_bytes};
+  return kohler_curve_batch(&im, 1, dt, M, nb, card, sumc, curve, cuda_stream);
+}
+
+int kohler_curve_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
+                       uint64_t* card, uint64_t* sumc, double* curve, void* cuda_stream) {
+  int rc = validate_batch(imgs, n, dt, M, nb);
+  if (rc) return rc;
+  if (n == 0) return KOHLER_OK;
+  if (!card || !sumc) return KOHLER_ERR_ARG;
+  return run_batch(imgs, n, dt, M, 0, card, sumc, curve, nullptr, nullptr, nullptr, (cudaStream_t)cuda_stream,
+                   nullptr);
+}
+
+int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
+                         int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
+                         int32_t* out_count, int32_t* out_t0, void* cuda_stream) {
+  int rc = validate_batch(imgs, n, dt, M, nb);
+  if (rc) return rc;
+  if (n == 0) return KOHLER_OK;
+  if (!card || !sumc || max_k < 0 || (max_k > 0 && !out_t) || !out_count || !out_t0) return KOHLER_ERR_ARG;
+  return run_batch(imgs, n, dt, M, max_k, card, sumc, curve, out_t, out_count, out_t0, (cudaStream_t)cuda_stream,
+                   nullptr);
+}
+
+int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int32_t M, int32_t max_k,
+                      int32_t* out_t, int32_t* out_count, int32_t* out_t0, void* cuda_stream) {
+  if (n < 0 || M < 1 || M > 65536 || max_k < 0) return KOHLER_ERR_ARG;
+  if (n == 0) return KOHLER_OK;
+  if (!card || !sumc || !out_count || !out_t0 || (max_k > 0 && !out_t)) return KOHLER_ERR_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const int cand_stride = (M + 1) / 2 + 2;
+  Workspace* ws = nullptr;
+  int rc = get_workspace(stream, kMaxBatch, 32, cand_stride, &ws);
+  if (rc) return rc;
+  for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
+    const int cn = std::min(kMaxBatch, n - c0);
+    ThreshParams Q;
+    Q.card = card + (size_t)c0 * M;
+    Q.sumc = sumc + (size_t)c0 * M;
+    Q.M = M;
+    Q.max_k = max_k;
+    Q.out_t = max_k > 0 ? out_t + (size_t)c0 * max_k : nullptr;
+    Q.out_count = out_count + c0;
+    Q.out_t0 = out_t0 + c0;
+    Q.cand = ws->cand;
+    Q.cand_stride = ws->cand_stride;
+    const size_t smem = epilogue_smem(M, 32, 0);
+    const size_t cs = (size_t)2 * M * 8 + (((size_t)(M + 1) / 2 + 2) * 4 + 15) / 16 * 16;
+    Q.staged = smem >= cs ? 1 : 0;
+    const size_t dyn = Q.staged ? cs : 0;
+    if (dyn > 48 * 1024) cudaFuncSetAttribute((const void*)k_thresholds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    k_thresholds<<<cn, kEpiThreads, dyn, stream>>>(Q);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return status_of(e);
+  }
+  return KOHLER_OK;
+}
+
+int kohler_stream_status(void* cuda_stream) {
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return status_of(e);
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    auto it = g_ws.find(std::make_pair(dev, (uintptr_t)stream));
+    if (it != g_ws.end()) w = it->second;
+  }
+  if (!w || !w->mem) return KOHLER_OK;
+  unsigned bits = 0;
+  e = cudaMemcpy(&bits, w->sticky, sizeof(bits), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return status_of(e);
+  if (bits) {
+    e = cudaMemset(w->sticky, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return status_of(e);
+  }
+  if (bits & kErrInternal) return KOHLER_ERR_CUDA;
+  return (bits & kErrRange) ? KOHLER_ERR_RANGE : KOHLER_OK;
+}
+
+int kohler_release(void) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  std::lock_guard<std::mutex> lock(g_mu);
+  for (auto it = g_ws.begin(); it != g_ws.end();) {
+    if (it->first.first == dev) {
+      if (it->second->mem) cudaFree(it->second->mem);
+      delete it->second;
+      it = g_ws.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  return KOHLER_OK;
+}
+
+const char* kohler_strerror(int status) {
+  switch (status) {
+    case KOHLER_OK: return "ok";
+    case KOHLER_PENDING: return "pending";
+    case KOHLER_ERR_ARG: return "invalid argument";
+    case KOHLER_ERR_UNSUPPORTED: return "unsupported";
+    case KOHLER_ERR_RANGE: return "pixel value >= M";
+    case KOHLER_ERR_NOMEM: return "out of memory";
+    case KOHLER_ERR_CUDA: return "CUDA error";
+    case KOHLER_ERR_TIMEOUT: return "timeout";
+    case KOHLER_ERR_BUSY: return "busy";
+  }
+  return "unknown status";
+}
+
+// ----------------------------------------------------------------------------- host-buffer path
+namespace {
+struct HostPath {
+  int device = -1;
+  cudaStream_t compute = nullptr, copy = nullptr;
+  void* dimg = nullptr;
+  size_t dimg_bytes = 0;
+  void* dout = nullptr;
+  size_t dout_bytes = 0;
+  std::vector<cudaEvent_t> ev;
+};
+std::mutex g_host_mu;
+std::map<int, HostPath*> g_host;
+
+int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  HostPath*& h = g_host[dev];
+  if (!h) {
+    h = new HostPath();
+    h->device = dev;
+    if ((e = cudaStreamCreateWithFlags(&h->compute, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
+    if ((e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
+  }
+  if (h->dimg_bytes < img_bytes) {
+    if (h->dimg) cudaFree(h->dimg);
+    h->dimg = nullptr;
+    h->dimg_bytes = 0;
+    if ((e = cudaMalloc(&h->dimg, img_bytes + 64)) != cudaSuccess) return status_of(e);
+    h->dimg_bytes = img_bytes;
+  }
+  if (h->dout_bytes < out_bytes) {
+    if (h->dout) cudaFree(h->dout);
+    h->dout = nullptr;
+    h->dout_bytes = 0;
+    if ((e = cudaMalloc(&h->dout, out_bytes)) != cudaSuccess) return status_of(e);
+    h->dout_bytes = out_bytes;
+  }
+  while ((int)h->ev.size() < bands) {
+    cudaEvent_t x;
+    if ((e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming)) != cudaSuccess) return status_of(e);
+    h->ev.push_back(x);
+  }
+  *out = h;
+  return KOHLER_OK;
+}
+}  // namespace
+
+int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
+                        int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve,
+                        int32_t* out_t, int32_t* out_count, int32_t* out_t0) {
+  int rc = check_common(dt, M, nb);
+  if (rc) return rc;
+  if (max_k < 0) return KOHLER_ERR_ARG;
+  rc = check_image(img, dt, width, height, pitch_bytes);
+  if (rc) return rc;
+  const int es = dt == KOHLER_U8 ? 1 : 2;
+  const int64_t dpitch = ((width * es + 127) / 128) * 128;  // device rows: aligned for the fast pass
+  const size_t img_bytes = (size_t)dpitch * height;
+  // device outputs: card, sumc (uint64 M), curve (double M), out_t (max_k), count, t0
+  const size_t o_card = 0, o_sumc = (size_t)M * 8, o_curve = 2 * (size_t)M * 8, o_t = 3 * (size_t)M * 8;
+  const size_t o_cnt = o_t + ((size_t)std::max(max_k, 1) * 4 + 15) / 16 * 16, o_t0 = o_cnt + 16;
+  const size_t out_bytes = o_t0 + 16;
+  // bands of rows: copy band b + 1 while band b is reduced (a band needs the first
+  // row of the next band for its lower pairs)
+  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  HostPath* h = nullptr;
+  rc = host_path(&h, img_bytes, out_bytes, nbands + 1);
+  if (rc) return rc;
+  char* dimg = static_cast<char*>(h->dimg);
+  char* dout = static_cast<char*>(h->dout);
+  std::vector<int32_t> yb(nbands + 1);
+  for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)((height * b) / nbands);
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < nbands && e == cudaSuccess; ++b) {
+    const int64_t r0 = yb[b], r1 = yb[b + 1];
+    if (r1 > r0)
+      e = cudaMemcpy2DAsync(dimg + r0 * dpitch, dpitch, static_cast<const char*>(img) + r0 * pitch_bytes, pitch_bytes,
+                            width * es, r1 - r0, cudaMemcpyHostToDevice, h->copy);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[b], h->copy);
+  }
+  if (e != cudaSuccess) return status_of(e);
+  kohler_image im{dimg, width, height, dpitch};
+  for (int b = 0; b < nbands; ++b) {
+    // band b reads rows [yb[b] - 1, yb[b + 1]]: wait for its own copy and the next one
+    e = cudaStreamWaitEvent(h->compute, h->ev[std::min(b + 1, nbands - 1)], 0);
+    if (e != cudaSuccess) return status_of(e);
+    std::vector<Band> band(1, Band{yb[b], yb[b + 1]});
+    if (yb[b + 1] <= yb[b]) continue;
+    rc = run_batch(&im, 1, dt, M, max_k, reinterpret_cast<uint64_t*>(dout + o_card),
+                   reinterpret_cast<uint64_t*>(dout + o_sumc), reinterpret_cast<double*>(dout + o_curve),
+                   max_k > 0 ? reinterpret_cast<int32_t*>(dout + o_t) : nullptr,
+                   reinterpret_cast<int32_t*>(dout + o_cnt), reinterpret_cast<int32_t*>(dout + o_t0), h->compute,
+                   &band);
+    if (rc) return rc;
+  }
+  // results back to the host
+  struct Cp {
+    void* dst;
+    size_t off, bytes;
+  } cps[] = {{card, o_card, (size_t)M * 8},   {sumc, o_sumc, (size_t)M * 8}, {curve, o_curve, (size_t)M * 8},
+             {out_t, o_t, (size_t)max_k * 4}, {out_count, o_cnt, 4},          {out_t0, o_t0, 4}};
+  for (auto& c : cps) {
+    if (!c.dst || c.bytes == 0) continue;
+    e = cudaMemcpyAsync(c.dst, dout + c.off, c.bytes, cudaMemcpyDeviceToHost, h->compute);
+    if (e != cudaSuccess) return status_of(e);
+  }
+  rc = kohler_stream_status(h->compute);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,991 @@
+// Device code of libkohler: the streaming pair-histogram pass, the exact scan
+// epilogue that turns the histograms into |B(t)| and the summed contrast for
+// every threshold, and the local-maximum threshold selection.
+//
+// Method (Section 2.1, Eq. 1-3; Section 3.2, Eq. 7-9).  Every unordered
+// 4-neighbour pair {p, q} (right and lower neighbour of each pixel: the half
+// neighbourhood N4*) with lo = min(f(p), f(q)), hi = max(...) adds 1 to |B(t)|
+// and min(hi - t, t - lo) to the summed contrast for each t in [lo, hi[.  With
+// the three histograms of the pairs' lo, hi and s = lo + hi,
+//   card(t) = #{lo <= t} - #{hi <= t}
+//   sumc(t) = sum (t - lo)_+ + sum (t - hi)_+ - sum (2t - s)_+
+// because min(hi - t, t - lo) on [lo, hi[ (and 0 elsewhere) is the tent
+// (t - lo)_+ + (t - hi)_+ - (2t - s)_+.  Pairs with lo = hi add 0 to both curves
+// whatever t, so they may be counted or not, as long as all three histograms
+// agree.  This replaces the per-pair loop over t of Algorithm 1 (cost O(N M))
+// by one histogram update per pair plus O(M) scans.
+//
+// The lo/hi histograms are accumulated per PIXEL: pixel p is the lo end of
+// n_lo(p) of its pairs and the hi end of deg(p) - n_lo(p), where deg(p) is its
+// number of in-image 4-neighbours.  So one shared-memory update per pixel
+// (value f(p), payload n_lo(p) and a pixel count) gives H_lo and, with the
+// border deficits, H_hi = 4 * count - border - H_lo.  Only the s histogram
+// needs one update per pair.  Ties (f(p) = f(q)) take the first pixel of the
+// pair as lo, which keeps equal pairs complete in all three histograms.
+//
+// Exactness: all counts are integers; the epilogue works in uint64 (every
+// intermediate is < 2^63 for images below 2^40 pixels).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace kohler {
+
+constexpr int kMaxBatch = 64;       // images per launch (descriptors travel in kernel parameters)
+constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
+
+enum ErrBits : unsigned { kErrRange = 1u, kErrInternal = 2u };
+
+struct ImgDesc {
+  const unsigned char* base;  // pixel (0, 0)
+  int64_t pitch;              // bytes between rows
+  int64_t rs_begin;           // first row-strip index of this image in the launch
+  int32_t W, H;               // full image size (borders are decided on it)
+  int32_t y0, y1;             // rows reduced by this launch: [y0, y1[ (a band of the image)
+  int32_t strips;             // column strips of the kernel's strip width
+  int32_t slot;               // workspace slot (histograms, counters)
+  int32_t out;                // index into the output arrays
+  int32_t pad_;
+};
+
+struct LaunchParams {
+  int32_t n;                  // images in this launch
+  int32_t M;                  // number of grey levels
+  int32_t bins;               // histogram bins per value axis (>= M)
+  int32_t max_k;              // thresholds per image (fused mode)
+  int64_t total_rs;           // row-strips over all images
+  // outputs (device)
+  uint64_t* card;             // [out][M]
+  uint64_t* sumc;             // [out][M]
+  double* curve;              // [out][M] or null
+  int32_t* out_t;             // [out][max_k] or null
+  int32_t* out_count;         // [out] or null: thresholds are computed when non-null
+  int32_t* out_t0;            // [out] or null
+  int32_t* out_status;        // [out] or null: KOHLER_OK or KOHLER_ERR_RANGE per image
+  // workspace (device)
+  unsigned long long* hist;   // [slot][4 * bins]: H_lo[bins], H_hi[bins], H_s[2 * bins]
+  unsigned int* done;         // [slot] row-strips reduced so far
+  unsigned int* err;          // [slot] error bits of the image
+  unsigned int* sticky;       // error bits of the stream (read by kohler_stream_status)
+  int32_t* cand;              // [slot][cand_stride] threshold candidates scratch
+  int32_t cand_stride;
+  int32_t smem_bytes;         // dynamic shared memory of the launch (reused by the epilogue)
+  ImgDesc img[kMaxBatch];
+};
+
+// ----------------------------------------------------------------------------- small helpers
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t r;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Exact comparison of sumc(a)/card(a) with sumc(b)/card(b) (both cards > 0):
+// sign of sumc(a) * card(b) - sumc(b) * card(a) over 128-bit products.
+__device__ __forceinline__ int cmp_ratio(uint64_t sa, uint64_t ca, uint64_t sb, uint64_t cb) {
+  uint64_t l_lo = sa * cb, l_hi = __umul64hi(sa, cb);
+  uint64_t r_lo = sb * ca, r_hi = __umul64hi(sb, ca);
+  if (l_hi != r_hi) return l_hi > r_hi ? 1 : -1;
+  if (l_lo != r_lo) return l_lo > r_lo ? 1 : -1;
+  return 0;
+}
+
+// Block-wide exclusive scan of one uint64 per thread (blockDim.x <= 1024, multiple of 32).
+// `scratch` holds 33 entries.  Returns the exclusive prefix; *total gets the block sum.
+__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* scratch, uint64_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) scratch[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint64_t w = lane < nw ? scratch[lane] : 0;
+    uint64_t s = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < nw) scratch[lane] = s - w;  // exclusive warp offsets
+    if (lane == 31) scratch[32] = s;
+  }
+  __syncthreads();
+  uint64_t r = scratch[warp] + x - v;
+  *total = scratch[32];
+  __syncthreads();
+  return r;
+}
+
+// ----------------------------------------------------------------------------- epilogue
+template <bool GLOBAL>
+__device__ __forceinline__ uint64_t ldh(const unsigned long long* p) {
+  return GLOBAL ? __ldcg(p) : *p;
+}
+
+// Curve of one image from its three histograms (one block, blockDim.x threads).
+// card(t)  = cumL(t) - cumH(t)
+// sumc(t)  = RLH(t) - RS(t),  RLH(t) = sum_{u < t} (cumL(u) + cumH(u)),
+//            RS(t) = sum_{1 <= u <= t} (2 cumS(2u - 2) + H_s(2u - 1))
+// where cumX are inclusive prefix sums.  H_GLOBAL: histograms in global memory
+// (read through L2), else in shared memory.  Writes card and sumc to both
+// (card_o, sumc_o: global outputs; card_s, sumc_s: optional shared copies) and
+// curve (if non-null).  When `bad` the outputs are all zero.
+template <bool H_GLOBAL>
+__device__ void curve_epilogue(const unsigned long long* hlo, const unsigned long long* hhi,
+                               const unsigned long long* hs, int M, bool bad, uint64_t* __restrict__ card_o,
+                               uint64_t* __restrict__ sumc_o, double* __restrict__ curve, uint64_t* card_s,
+                               uint64_t* sumc_s, uint64_t* scratch) {
+  const int nt = blockDim.x;
+  const int chunk = (M + nt - 1) / nt;
+  const int c0 = min(M, (int)threadIdx.x * chunk), c1 = min(M, c0 + chunk);
+  const int S = 2 * M - 1;  // s in [0, 2M - 2]
+  // pass 1: chunk sums of H_lo, H_hi, and of H_s over u in [2 c0, 2 c1)
+  uint64_t sl = 0, sh = 0, ss = 0;
+  for (int t = c0; t < c1; ++t) {
+    sl += ldh<H_GLOBAL>(hlo + t);
+    sh += ldh<H_GLOBAL>(hhi + t);
+  }
+  for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL>(hs + u);
+  uint64_t tot;
+  const uint64_t baseL = block_excl_scan(sl, scratch, &tot);
+  const uint64_t baseH = block_excl_scan(sh, scratch, &tot);
+  const uint64_t baseS = block_excl_scan(ss, scratch, &tot);  // sum of H_s over u < 2 c0
+  // pass 2: chunk sums of cumA = cumL + cumH and of g(t) = 2 cumS(2t - 2) + H_s(2t - 1)
+  uint64_t sa = 0, sg = 0;
+  {
+    uint64_t cl = baseL, ch = baseH;
+    // cumS_excl(u) = sum_{v < u} H_s(v); start at u = 2 c0 - 1
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
+    uint64_t cs_excl = baseS - hprev;  // cumS_excl(2 c0 - 1)
+    for (int t = c0; t < c1; ++t) {
+      cl += ldh<H_GLOBAL>(hlo + t);
+      ch += ldh<H_GLOBAL>(hhi + t);
+      sa += cl + ch;
+      if (t > 0) {
+        const uint64_t h1 = ldh<H_GLOBAL>(hs + 2 * t - 1);
+        sg += 2 * cs_excl + h1;  // 2 cumS(2t - 2) + H_s(2t - 1)
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL>(hs + 2 * t) : 0);  // -> cumS_excl(2t + 1)
+      } else {
+        cs_excl += (S > 0 ? ldh<H_GLOBAL>(hs + 0) : 0);  // cumS_excl(1)
+      }
+    }
+  }
+  const uint64_t baseA = block_excl_scan(sa, scratch, &tot);  // sum of cumA(u) for u < c0
+  const uint64_t baseG = block_excl_scan(sg, scratch, &tot);  // sum of g(u) for u < c0
+  // pass 3: outputs
+  {
+    uint64_t cl = baseL, ch = baseH, rlh = baseA, rs = baseG;
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
+    uint64_t cs_excl = baseS - hprev;
+    for (int t = c0; t < c1; ++t) {
+      cl += ldh<H_GLOBAL>(hlo + t);
+      ch += ldh<H_GLOBAL>(hhi + t);
+      if (t > 0) {
+        const uint64_t h1 = ldh<H_GLOBAL>(hs + 2 * t - 1);
+        rs += 2 * cs_excl + h1;
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL>(hs + 2 * t) : 0);
+      } else {
+        cs_excl += (S > 0 ? ldh<H_GLOBAL>(hs + 0) : 0);
+      }
+      const uint64_t k = bad ? 0 : cl - ch;
+      const uint64_t sm = bad ? 0 : rlh - rs;
+      card_o[t] = k;
+      sumc_o[t] = sm;
+      if (card_s) {
+        card_s[t] = k;
+        sumc_s[t] = sm;
+      }
+      if (curve) curve[t] = k ? (double)sm / (double)k : 0.0;
+      rlh += cl + ch;  // RLH(t + 1) = RLH(t) + cumA(t)
+    }
+  }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- thresholds
+// Local maxima of C(t) = sumc/card among thresholds with card > 0, ranked by C
+// descending then t ascending; t0 = first t with the largest C (Eq. 4).
+// One block.  `cand` is scratch for up to (M + 1) / 2 + 1 candidates.
+__device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, int M, int max_k, int32_t* out_t,
+                                  int32_t* out_count, int32_t* out_t0, int32_t* cand, int* sh_int,
+                                  uint64_t* scratch) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) sh_int[0] = 0;
+  __syncthreads();
+  // 1. plateau starts that are local maxima
+  for (int t = tid; t < M; t += nt) {
+    const uint64_t ct = card[t];
+    if (ct == 0) continue;
+    const uint64_t st = sumc[t];
+    bool start = true, left_lower = true;
+    if (t > 0 && card[t - 1] > 0) {
+      const int c = cmp_ratio(sumc[t - 1], card[t - 1], st, ct);
+      start = c != 0;
+      left_lower = c < 0;
+    }
+    if (!start || !left_lower) continue;
+    int b = t;
+    while (b + 1 < M && card[b + 1] > 0 && cmp_ratio(sumc[b + 1], card[b + 1], st, ct) == 0) ++b;
+    const bool right_lower = (b + 1 >= M) || card[b + 1] == 0 || cmp_ratio(sumc[b + 1], card[b + 1], st, ct) < 0;
+    if (right_lower) cand[atomicAdd(&sh_int[0], 1)] = t;
+  }
+  __syncthreads();
+  const int K = sh_int[0];
+  // 2. t0 (Eq. 4): best (C, -t) over valid t, block reduction via candidates is not
+  //    enough in general (t0 is always a local maximum, but compute it directly).
+  int best = -1;
+  for (int t = tid; t < M; t += nt) {
+    if (card[t] == 0) continue;
+    if (best < 0) { best = t; continue; }
+    const int c = cmp_ratio(sumc[t], card[t], sumc[best], card[best]);
+    if (c > 0) best = t;  // t increases within a thread, so ties keep the smaller t
+  }
+  // warp + block reduction of `best`
+  for (int o = 16; o > 0; o >>= 1) {
+    const int other = __shfl_down_sync(0xffffffffu, best, o);
+    if (other >= 0) {
+      if (best < 0) best = other;
+      else {
+        const int c = cmp_ratio(sumc[other], card[other], sumc[best], card[best]);
+        if (c > 0 || (c == 0 && other < best)) best = other;
+      }
+    }
+  }
+  int* wbest = sh_int + 1;
+  if ((tid & 31) == 0) wbest[tid >> 5] = best;
+  __syncthreads();
+  if (tid == 0) {
+    int b = -1;
+    for (int w = 0; w < nt / 32; ++w) {
+      const int o = wbest[w];
+      if (o < 0) continue;
+      if (b < 0) b = o;
+      else {
+        const int c = cmp_ratio(sumc[o], card[o], sumc[b], card[b]);
+        if (c > 0 || (c == 0 && o < b)) b = o;
+      }
+    }
+    if (out_t0) *out_t0 = b;
+    if (out_count) *out_count = K;
+  }
+  // 3. rank each candidate: number of candidates that come before it
+  for (int i = tid; i < K; i += nt) {
+    const int ti = cand[i];
+    const uint64_t si = sumc[ti], ci = card[ti];
+    int rank = 0;
+    for (int j = 0; j < K && rank < max_k; ++j) {
+      const int tj = cand[j];
+      if (tj == ti) continue;
+      const int c = cmp_ratio(sumc[tj], card[tj], si, ci);
+      if (c > 0 || (c == 0 && tj < ti)) ++rank;
+    }
+    if (rank < max_k && out_t) out_t[rank] = ti;
+  }
+  for (int r = K + tid; r < max_k; r += nt)
+    if (out_t) out_t[r] = -1;
+  __syncthreads();
+}
+
+// Final step of an image: called by the block that observed the image's last
+// row-strips arrive.  Reads the three global histograms, writes the outputs,
+// zeroes the histograms and the counters for the next launch.  `dsm` is the
+// block's dynamic shared memory (`dsm_bytes`), free at this point: the
+// histograms, card/sumc and the threshold candidates are staged there when they
+// fit, so the scans and the threshold search run on shared memory.
+__device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, int* sh_int, unsigned char* dsm,
+                             size_t dsm_bytes) {
+  const ImgDesc& d = P.img[i];
+  const int M = P.M, bins = P.bins;
+  unsigned long long* h = P.hist + (size_t)d.slot * 4 * bins;
+  __threadfence();
+  const bool bad = (__ldcg(P.err + d.slot) & kErrRange) != 0;
+  uint64_t* card = P.card + (size_t)d.out * M;
+  uint64_t* sumc = P.sumc + (size_t)d.out * M;
+  double* curve = P.curve ? P.curve + (size_t)d.out * M : nullptr;
+  const size_t need_cs = (size_t)2 * M * 8, need_cand = ((size_t)(M + 1) / 2 + 2) * 4;
+  const size_t need_h = (size_t)4 * bins * 8;
+  const bool stage_cs = dsm_bytes >= need_cs + need_cand;
+  const bool stage_h = dsm_bytes >= need_cs + need_cand + need_h;
+  uint64_t* card_s = stage_cs ? reinterpret_cast<uint64_t*>(dsm) : nullptr;
+  uint64_t* sumc_s = stage_cs ? card_s + M : nullptr;
+  int32_t* cand = stage_cs ? reinterpret_cast<int32_t*>(dsm + need_cs) : P.cand + (size_t)d.slot * P.cand_stride;
+  if (stage_h) {
+    unsigned long long* hsm = reinterpret_cast<unsigned long long*>(dsm + ((need_cs + need_cand + 15) & ~(size_t)15));
+    for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) {
+      hsm[b] = __ldcg(h + b);
+      h[b] = 0ull;  // clean the workspace slot for the next use
+    }
+    __syncthreads();
+    curve_epilogue<false>(hsm, hsm + bins, hsm + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
+  } else {
+    curve_epilogue<true>(h, h + bins, h + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
+    for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) h[b] = 0ull;
+  }
+  if (P.out_count) {
+    select_thresholds(stage_cs ? card_s : card, stage_cs ? sumc_s : sumc, M, P.max_k,
+                      P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr, P.out_count + d.out,
+                      P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
+  }
+  if (threadIdx.x == 0) {
+    if (P.out_status) P.out_status[d.out] = bad ? -3 : 0;  // KOHLER_ERR_RANGE / KOHLER_OK
+    if (bad) atomicOr(P.sticky, kErrRange);
+    P.err[d.slot] = 0u;
+    P.done[d.slot] = 0u;
+  }
+  __syncthreads();
+}
+
+// Adds `n` finished row-strips to image i; the block that completes the image
+// runs finish_image.  Must be called by all threads of the block after their
+// global histogram updates.
+__device__ void image_rows_done(const LaunchParams& P, int i, int64_t n, uint64_t* scratch, int* sh_int,
+                                unsigned char* dsm, size_t dsm_bytes) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const ImgDesc& d = P.img[i];
+    const unsigned total = (unsigned)((int64_t)d.strips * d.H);  // all bands of the image
+    const unsigned prev = atomicAdd(P.done + d.slot, (unsigned)n);
+    sh_int[0] = (prev + (unsigned)n == total) ? 1 : 0;
+  }
+  __syncthreads();
+  const bool last = sh_int[0] != 0;
+  __syncthreads();
+  if (last) finish_image(P, i, scratch, sh_int, dsm, dsm_bytes);
+}
+
+// Image containing global row-strip r (linear search; n <= kMaxBatch).  Images
+// with an empty band hold no row-strip and are skipped by the search.
+__device__ __forceinline__ int image_of(const LaunchParams& P, int64_t r) {
+  int i = 0;
+  while (i + 1 < P.n && P.img[i + 1].rs_begin <= r) ++i;
+  return i;
+}
+
+// ----------------------------------------------------------------------------- uint16 pass traits
+// Pixels travel as pairs of 16-bit lanes in 32-bit registers.  For a pair
+// (first -> second), second + BIAS - first has bit log2(BIAS) of each lane set
+// iff second >= first, with no borrow between lanes (values < BIAS).
+struct TraitsU16 {
+  static constexpr int PX = 4;
+  static constexpr int NV = 2;
+  static constexpr uint32_t BIAS = 0x10001000u;  // values clamped below 4096
+  static constexpr int SHIFT = 12;
+  static constexpr int ELEM = 2;
+  static __device__ __forceinline__ void unpack(uint2 raw, uint32_t (&v)[NV]) {
+    v[0] = raw.x;
+    v[1] = raw.y;
+  }
+};
+
+template <int ELEM>
+__device__ __forceinline__ uint2 load8(const unsigned char* p) {
+  return __ldg(reinterpret_cast<const uint2*>(p));
+}
+
+// Flush the CTA's shared histograms of image i into its global slot and clear them.
+__device__ __forceinline__ void flush_cta(const LaunchParams& P, int i, uint32_t* hs, uint32_t* lo, uint32_t* cnt,
+                                          int32_t* brd, int bins) {
+  unsigned long long* g = P.hist + (size_t)P.img[i].slot * 4 * bins;
+  for (int b = threadIdx.x; b < bins; b += blockDim.x) {
+    const uint32_t l = lo[b], c = cnt[b];
+    const int32_t r = brd[b];
+    const long long hi = 4ll * (long long)c - (long long)r - (long long)l;
+    if (l) atomicAdd(g + b, (unsigned long long)l);
+    if (hi) atomicAdd(g + bins + b, (unsigned long long)hi);
+    lo[b] = 0u;
+    cnt[b] = 0u;
+    brd[b] = 0;
+  }
+  for (int b = threadIdx.x; b < 2 * bins; b += blockDim.x) {
+    const uint32_t s = hs[b];
+    if (s) atomicAdd(g + 2 * bins + b, (unsigned long long)s);
+    hs[b] = 0u;
+  }
+}
+
+// ----------------------------------------------------------------------------- uint16 pass
+// Each warp walks a run of rows of one column strip (32 lanes x PX pixels).
+// Lane registers hold the current row V and the next row N as 16x2 lanes;
+// per row it forms the right pairs (V, R) and the lower pairs (V, N), updates
+// the s histogram once per pair and the pixel count / n_lo bins once per pixel
+// (block-wide 32-bit bins: 4096 values are too many for per-warp copies).
+// Requirements (checked on the host): W % PX == 0, base and pitch multiples of 8.
+template <class T, int NW, bool CHECK>
+__global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ LaunchParams P) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  constexpr int PX = T::PX, NV = T::NV;
+  constexpr uint32_t BIAS = T::BIAS;
+  const int bins = P.bins;
+  uint32_t* hs = smem;
+  uint32_t* lo = hs + 2 * bins;
+  uint32_t* cnt = lo + bins;
+  int32_t* brd = reinterpret_cast<int32_t*>(cnt + bins);
+  __shared__ uint64_t scratch[40];
+  __shared__ int sh_int[40];
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const size_t words = (size_t)bins * 5;
+  for (size_t k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+  __syncthreads();
+
+  const uint32_t mclamp = (uint32_t)(P.M - 1) | ((uint32_t)(P.M - 1) << 16);
+  const int64_t T_all = P.total_rs;
+  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
+  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
+  int i = r0 < r1 ? image_of(P, r0) : 0;
+
+  while (r0 < r1) {
+    const ImgDesc& d = P.img[i];
+    const int BH = d.y1 - d.y0;
+    const int64_t iend = d.rs_begin + (int64_t)d.strips * BH;
+    const int64_t seg_end = min(r1, iend);
+    const int64_t seg = seg_end - r0;
+    const int W = d.W, H = d.H;
+    const int64_t pitch = d.pitch;
+    uint32_t vmax = 0;
+    // this warp's share of the segment
+    int64_t a = r0 + (seg * warp) / NW;
+    const int64_t b = r0 + (seg * (warp + 1)) / NW;
+    while (a < b) {
+      const int64_t q = a - d.rs_begin;
+      const int strip = (int)(q / BH);
+      const int ya = d.y0 + (int)(q % BH);
+      const int yb = (int)min64((int64_t)d.y1, (int64_t)ya + (b - a));
+      a += yb - ya;
+      const int x0 = strip * (32 * PX) + lane * PX;
+      const bool act = x0 < W;
+      const bool lastlane = act && (x0 + PX == W);
+      const bool need_right = act && !lastlane && lane == 31;
+      const bool need_left = act && x0 > 0 && lane == 0;
+      const unsigned char* col = d.base + (int64_t)x0 * T::ELEM;
+      // one row of this lane: its PX pixels, plus (lane 31 / lane 0) the pixel just
+      // right / left of the strip, which the neighbouring strip's warp owns
+      auto load_row = [&](int yy, uint2& raw, uint32_t& edge) {
+        raw = make_uint2(0u, 0u);
+        edge = 0u;
+        if (act && yy < H) {
+          const unsigned char* pr = col + (int64_t)yy * pitch;
+          raw = load8<T::ELEM>(pr);
+          if (need_right) edge = (T::ELEM == 1) ? (uint32_t)__ldg(pr + PX) : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(pr + PX * 2));
+          if (need_left) edge = (T::ELEM == 1) ? (uint32_t)__ldg(pr - 1) : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(pr - 2));
+        }
+      };
+      uint32_t V[NV], N[NV], GEup[NV];
+      uint2 rc, pf0, pf1;
+      uint32_t ec, ef0, ef1;
+      load_row(ya, rc, ec);
+      load_row(ya + 1, pf0, ef0);
+      load_row(ya + 2 <= yb ? ya + 2 : H, pf1, ef1);
+      T::unpack(rc, V);
+      if (CHECK) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) { vmax = __vmaxu2(vmax, V[k]); V[k] = __vminu2(V[k], mclamp); }
+      }
+      if (ya > 0) {
+        uint2 ru;
+        uint32_t eu;
+        load_row(ya - 1, ru, eu);
+        uint32_t U[NV];
+        T::unpack(ru, U);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+          if (CHECK) U[k] = __vminu2(U[k], mclamp);
+          GEup[k] = (V[k] + BIAS - U[k]) & BIAS;  // pair (upper -> p): flag [f(p) >= f(upper)]
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) GEup[k] = BIAS;  // no upper pair: contributes nothing to n_lo
+      }
+      for (int y = ya; y < yb; ++y) {
+        const bool has_down = y + 1 < H;
+        const uint2 rn = pf0;
+        const uint32_t en = ef0;
+        pf0 = pf1;
+        ef0 = ef1;
+        load_row(y + 3 <= yb ? y + 3 : H, pf1, ef1);  // rows up to yb are needed (lower pairs of row yb - 1)
+        // neighbours across lanes of the current row
+        uint32_t rv = __shfl_down_sync(0xffffffffu, V[0], 1);    // its low lane: right neighbour
+        uint32_t lv = __shfl_up_sync(0xffffffffu, V[NV - 1], 1); // its high lane: left neighbour
+        if (need_right) rv = CHECK ? min(ec, (uint32_t)(P.M - 1)) : ec;
+        if (lastlane) rv = V[NV - 1] >> 16;  // no right pair: pad with an equal pair
+        if (lane == 0) {
+          // no left pair: a neighbour of value 0 gives flag 1, i.e. no n_lo
+          lv = need_left ? ((CHECK ? min(ec, (uint32_t)(P.M - 1)) : ec) << 16) : 0u;
+        }
+        T::unpack(rn, N);
+        if (CHECK) {
+#pragma unroll
+          for (int k = 0; k < NV; ++k) { vmax = __vmaxu2(vmax, N[k]); N[k] = __vminu2(N[k], mclamp); }
+        }
+        if (act) {
+          uint32_t R[NV], GEr[NV], GEd[NV];
+#pragma unroll
+          for (int k = 0; k < NV; ++k) R[k] = prmt(V[k], k + 1 < NV ? V[k + 1] : rv, 0x5432u);
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            GEr[k] = (R[k] + BIAS - V[k]) & BIAS;                    // pairs (p -> right)
+            GEd[k] = has_down ? ((N[k] + BIAS - V[k]) & BIAS) : 0u;  // pairs (p -> lower)
+          }
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            const uint32_t GEl = (k == 0) ? ((V[0] + BIAS - prmt(lv, V[0], 0x5432u)) & BIAS)
+                                          : prmt(GEr[k - 1], GEr[k], 0x5432u);
+            // n_lo(p) = [right >= p] + [lower >= p] + [left > p] + [upper > p], x BIAS
+            const uint32_t nlo = (GEr[k] + GEd[k] + 2u * BIAS) - (GEl + GEup[k]);
+            const uint32_t p0 = V[k] & 0xffffu, p1 = V[k] >> 16;
+            atomicAdd(&cnt[p0], 1u);
+            atomicAdd(&lo[p0], (nlo >> T::SHIFT) & 0xfu);
+            atomicAdd(&cnt[p1], 1u);
+            atomicAdd(&lo[p1], nlo >> (16 + T::SHIFT));
+            const uint32_t sr = V[k] + R[k];
+            atomicAdd(&hs[sr & 0xffffu], 1u);
+            atomicAdd(&hs[sr >> 16], 1u);
+            if (has_down) {
+              const uint32_t sd = V[k] + N[k];
+              atomicAdd(&hs[sd & 0xffffu], 1u);
+              atomicAdd(&hs[sd >> 16], 1u);
+            }
+          }
+          // border deficits: missing upper / lower / left neighbours add 1, the
+          // padded right pair of the last column subtracts 1 (its partner is absent)
+          const int rowb = (y == 0 ? 1 : 0) + (has_down ? 0 : 1);
+          if (rowb) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+              atomicAdd(&brd[V[k] & 0xffffu], rowb);
+              atomicAdd(&brd[V[k] >> 16], rowb);
+            }
+          }
+          if (x0 == 0) atomicAdd(&brd[V[0] & 0xffffu], 1);
+          if (lastlane) atomicAdd(&brd[V[NV - 1] >> 16], -1);
+#pragma unroll
+          for (int k = 0; k < NV; ++k) {
+            GEup[k] = GEd[k];
+            V[k] = N[k];
+          }
+        }
+        ec = en;
+      }
+    }
+    if (CHECK && ((vmax & 0xffffu) >= (uint32_t)P.M || (vmax >> 16) >= (uint32_t)P.M)) atomicOr(P.err + d.slot, kErrRange);
+    __syncthreads();
+    flush_cta(P, i, hs, lo, cnt, brd, bins);
+    __syncthreads();
+    image_rows_done(P, i, seg, scratch, sh_int, reinterpret_cast<unsigned char*>(smem), (size_t)P.smem_bytes);
+    // the epilogue may have used the shared histograms as scratch: clear them again
+    for (size_t k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+    __syncthreads();
+    r0 = seg_end;
+    ++i;
+  }
+}
+
+// ----------------------------------------------------------------------------- uint8 pass
+// The uint8 pass, written for few instructions per pixel.  A lane holds 8
+// pixels of a row, split into four registers of two 16-bit lanes:
+//   E0 = (p0, p2), O0 = (p1, p3), E1 = (p4, p6), O1 = (p5, p7),
+// each value multiplied by 4, so that register halves are ready-made byte
+// offsets of 32-bit shared-memory bins.  The right pairs of the row are then
+// (E0 -> O0), (O0 -> (p2, p4)), (E1 -> O1), (O1 -> (p6, p8)): two of the four
+// "right" registers are free and the other two take one byte permute each.
+// Flags use a bias of 1024 (values * 4 <= 1020).  Per-pixel bins are per warp
+// and packed (low 16 bits: 4 * n_lo, high 16 bits: pixel count); a warp
+// flushes them into the block's 32-bit totals every kPackRows rows.
+namespace u8 {
+constexpr uint32_t B = 0x04000400u;   // bias per 16-bit lane
+constexpr uint32_t LOW = 0x00ff00ffu;
+constexpr uint32_t LOW4 = 0x03fc03fcu;
+constexpr int kPackRows = 15;         // 15 rows * 256 px * 16 < 65536
+constexpr int kWords = 512 + 3 * 256; // hs[512], lo[256], cnt[256], brd[256]; then pk[NW][256]
+
+// Shared-memory add at a 32-bit shared-window address (no return value).
+__device__ __forceinline__ void red_s(uint32_t addr, uint32_t v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+struct Row {
+  uint32_t E0, O0, E1, O1;  // 4 * (p0,p2), 4 * (p1,p3), 4 * (p4,p6), 4 * (p5,p7)
+};
+
+__device__ __forceinline__ Row unpack(uint2 r) {
+  Row v;
+  v.E0 = (r.x << 2) & LOW4;
+  v.O0 = (r.x >> 6) & LOW4;
+  v.E1 = (r.y << 2) & LOW4;
+  v.O1 = (r.y >> 6) & LOW4;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t ge(uint32_t second, uint32_t first) { return (second + B - first) & B; }
+}  // namespace u8
+
+template <int NW, bool CHECK>
+__global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchParams P) {
+  using namespace u8;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint64_t scratch[40];
+  __shared__ int sh_int[40];
+  unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
+  uint32_t* const hs = smem;        // byte offset 0
+  uint32_t* const lo = smem + 512;  // 2048
+  uint32_t* const cnt = smem + 768; // 3072
+  int32_t* const brd = reinterpret_cast<int32_t*>(smem + 1024);  // 4096
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // shared-window addresses fit 16 bits: add them to both lanes of a key register
+  const int words = kWords + NW * 256;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t pk_addr = sbase + (uint32_t)(kWords + warp * 256) * 4u;
+  const uint32_t PK2 = pk_addr | (pk_addr << 16);
+  const uint32_t HS2 = sbase | (sbase << 16);
+  if (sbase + (uint32_t)words * 4u >= 65536u) {  // shared addresses are block-relative and small
+    if (threadIdx.x == 0) atomicOr(P.sticky, kErrInternal);
+    return;
+  }
+  uint32_t* const mypk = smem + kWords + warp * 256;
+  for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+  __syncthreads();
+  const uint32_t clamp4 = CHECK ? (uint32_t)(4 * (P.M - 1)) * 0x00010001u : 0u;
+
+  const int64_t T_all = P.total_rs;
+  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
+  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
+  int i = r0 < r1 ? image_of(P, r0) : 0;
+  while (r0 < r1) {
+    const ImgDesc& d = P.img[i];
+    const int BH = d.y1 - d.y0;
+    const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * BH);
+    const int64_t seg = seg_end - r0;
+    const int W = d.W, H = d.H;
+    const int64_t pitch = d.pitch;
+    uint32_t vmax = 0;
+    int pack_rows = 0;
+    int64_t a = r0 + (seg * warp) / NW;
+    const int64_t b = r0 + (seg * (warp + 1)) / NW;
+    while (a < b) {
+      const int64_t q = a - d.rs_begin;
+      const int strip = (int)(q / BH);
+      const int ya = d.y0 + (int)(q % BH);
+      const int yb = (int)min64((int64_t)d.y1, (int64_t)ya + (b - a));
+      a += yb - ya;
+      const int x0 = strip * 256 + lane * 8;
+      const bool act = x0 < W;
+      const bool lastlane = act && (x0 + 8 == W);
+      const bool need_right = act && !lastlane && lane == 31;
+      const bool need_left = act && x0 > 0 && lane == 0;
+      const bool edge_warp = (strip == 0) || ((strip + 1) * 256 >= W);  // holds x = 0 or x = W - 1
+      const unsigned char* rowp = d.base + (int64_t)ya * pitch + x0;
+      // prefetch ring: rows ya (current), ya + 1, ya + 2
+      auto ld = [&](const unsigned char* p, bool ok, uint2& raw, uint32_t& edge) {
+        raw = make_uint2(0u, 0u);
+        edge = 0u;
+        if (ok && act) {
+          raw = __ldg(reinterpret_cast<const uint2*>(p));
+          if (need_right) edge = __ldg(p + 8);
+          if (need_left) edge = __ldg(p - 1);
+        }
+      };
+      uint2 rc, pf0, pf1;
+      uint32_t ec, ef0, ef1;
+      ld(rowp, true, rc, ec);
+      ld(rowp + pitch, ya + 1 < H, pf0, ef0);
+      ld(rowp + 2 * pitch, ya + 2 < H && ya + 2 <= yb, pf1, ef1);
+      Row V = unpack(rc);
+      if (CHECK) {
+        vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V.E0, V.O0)), __vmaxu2(V.E1, V.O1));
+        V.E0 = __vminu2(V.E0, clamp4); V.O0 = __vminu2(V.O0, clamp4);
+        V.E1 = __vminu2(V.E1, clamp4); V.O1 = __vminu2(V.O1, clamp4);
+      }
+      uint32_t UE0 = B, UO0 = B, UE1 = B, UO1 = B;  // flags of pairs (upper -> p); B: no upper pair
+      if (ya > 0) {
+        uint2 ru;
+        uint32_t eu;
+        ld(rowp - pitch, true, ru, eu);
+        Row U = unpack(ru);
+        if (CHECK) {
+          U.E0 = __vminu2(U.E0, clamp4); U.O0 = __vminu2(U.O0, clamp4);
+          U.E1 = __vminu2(U.E1, clamp4); U.O1 = __vminu2(U.O1, clamp4);
+        }
+        UE0 = ge(V.E0, U.E0); UO0 = ge(V.O0, U.O0); UE1 = ge(V.E1, U.E1); UO1 = ge(V.O1, U.O1);
+      }
+      for (int y = ya; y < yb; ++y) {
+        const bool has_down = y + 1 < H;
+        const uint2 rn = pf0;
+        const uint32_t en = ef0;
+        pf0 = pf1;
+        ef0 = ef1;
+        ld(rowp + 3 * pitch, y + 3 < H && y + 3 <= yb, pf1, ef1);
+        Row N = unpack(rn);
+        if (CHECK) {
+          vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(N.E0, N.O0)), __vmaxu2(N.E1, N.O1));
+          N.E0 = __vminu2(N.E0, clamp4); N.O0 = __vminu2(N.O0, clamp4);
+          N.E1 = __vminu2(N.E1, clamp4); N.O1 = __vminu2(N.O1, clamp4);
+        }
+        // right neighbour of p7: p0 of the next lane, the next strip's first pixel,
+        // or (last column) p7 itself, which pads the missing pair with an equal one
+        uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
+        if (need_right) nb = CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2;
+        if (lastlane) nb = V.O1 >> 16;
+        const uint32_t E0s = prmt(V.E0, V.E1, 0x5432u);  // (p2, p4)
+        const uint32_t E1s = prmt(V.E1, nb, 0x5432u);    // (p6, p8)
+        // flags [second >= first] of the right pairs, per register of first pixels
+        const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
+        // lower pairs
+        uint32_t DE0 = 0, DO0 = 0, DE1 = 0, DO1 = 0;
+        if (has_down) { DE0 = ge(N.E0, V.E0); DO0 = ge(N.O0, V.O0); DE1 = ge(N.E1, V.E1); DO1 = ge(N.O1, V.O1); }
+        // pair (p-1 -> p0): from the previous lane's last right pair, or the left
+        // strip's last pixel (value 0 at x = 0: flag 1, i.e. no contribution)
+        uint32_t gl = __shfl_up_sync(0xffffffffu, GO1, 1);
+        if (lane == 0) {
+          const uint32_t el4 = need_left ? (CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2) : 0u;
+          gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
+        }
+        const uint32_t LE0 = prmt(gl, GO0, 0x5432u);   // pairs ending at p0, p2
+        const uint32_t LE1 = prmt(GO0, GO1, 0x5432u);  // pairs ending at p4, p6
+        // n_lo * 1024 per pixel: [right >= p] + [lower >= p] + [left > p] + [upper > p]
+        const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
+        const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
+        const uint32_t nE1 = (GE1 + DE1 + 2 * B) - (LE1 + UE1);
+        const uint32_t nO1 = (GO1 + DO1 + 2 * B) - (GE1 + UO1);
+        if (act) {
+          // per-pixel packed bins: payload (4 n_lo) | (1 << 16)
+          const uint32_t aE0 = V.E0 + PK2, aO0 = V.O0 + PK2, aE1 = V.E1 + PK2, aO1 = V.O1 + PK2;
+          red_s(aE0 & 0xffffu, prmt(nE0, 0x00010000u, 0x7601u));
+          red_s(aE0 >> 16, prmt(nE0, 0x00010000u, 0x7603u));
+          red_s(aO0 & 0xffffu, prmt(nO0, 0x00010000u, 0x7601u));
+          red_s(aO0 >> 16, prmt(nO0, 0x00010000u, 0x7603u));
+          red_s(aE1 & 0xffffu, prmt(nE1, 0x00010000u, 0x7601u));
+          red_s(aE1 >> 16, prmt(nE1, 0x00010000u, 0x7603u));
+          red_s(aO1 & 0xffffu, prmt(nO1, 0x00010000u, 0x7601u));
+          red_s(aO1 >> 16, prmt(nO1, 0x00010000u, 0x7603u));
+          // pair sums s = f(p) + f(q): shared addresses of hs[s]
+          const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
+          const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
+          red_s(sE0 & 0xffffu, 1u);
+          red_s(sE0 >> 16, 1u);
+          red_s(sO0 & 0xffffu, 1u);
+          red_s(sO0 >> 16, 1u);
+          red_s(sE1 & 0xffffu, 1u);
+          red_s(sE1 >> 16, 1u);
+          red_s(sO1 & 0xffffu, 1u);
+          red_s(sO1 >> 16, 1u);
+          if (has_down) {
+            const uint32_t dE0 = V.E0 + N.E0 + HS2, dO0 = V.O0 + N.O0 + HS2;
+            const uint32_t dE1 = V.E1 + N.E1 + HS2, dO1 = V.O1 + N.O1 + HS2;
+            red_s(dE0 & 0xffffu, 1u);
+            red_s(dE0 >> 16, 1u);
+            red_s(dO0 & 0xffffu, 1u);
+            red_s(dO0 >> 16, 1u);
+            red_s(dE1 & 0xffffu, 1u);
+            red_s(dE1 >> 16, 1u);
+            red_s(dO1 & 0xffffu, 1u);
+            red_s(dO1 >> 16, 1u);
+          }
+          // border deficits 4 - deg(p); the padded right pair of the last column
+          // counts -1 (its partner is absent)
+          if (y == 0 || !has_down) {
+            const int rowb = (y == 0 ? 1 : 0) + (has_down ? 0 : 1);
+            const uint32_t vv[4] = {V.E0, V.O0, V.E1, V.O1};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              atomicAdd(&brd[(vv[k] & 0xffffu) >> 2], rowb);
+              atomicAdd(&brd[vv[k] >> 18], rowb);
+            }
+          }
+          if (edge_warp) {
+            if (x0 == 0) atomicAdd(&brd[(V.E0 & 0xffffu) >> 2], 1);
+            if (lastlane) atomicAdd(&brd[V.O1 >> 18], -1);
+          }
+        }
+        V = N;
+        UE0 = DE0; UO0 = DO0; UE1 = DE1; UO1 = DO1;
+        ec = en;
+        rowp += pitch;
+        if (++pack_rows == kPackRows) {
+          __syncwarp();
+          asm volatile("" ::: "memory");
+          for (int v = lane; v < 256; v += 32) {
+            const uint32_t w = mypk[v];
+            if (w) {
+              atomicAdd(&lo[v], (w & 0xffffu) >> 2);
+              atomicAdd(&cnt[v], w >> 16);
+              mypk[v] = 0u;
+            }
+          }
+          __syncwarp();
+          pack_rows = 0;
+        }
+      }
+    }
+    if (CHECK && ((vmax & 0xffffu) > 4u * (uint32_t)(P.M - 1) || (vmax >> 16) > 4u * (uint32_t)(P.M - 1)))
+      atomicOr(P.err + d.slot, kErrRange);
+    __syncwarp();
+    asm volatile("" ::: "memory");
+    for (int v = lane; v < 256; v += 32) {
+      const uint32_t w = mypk[v];
+      if (w) {
+        atomicAdd(&lo[v], (w & 0xffffu) >> 2);
+        atomicAdd(&cnt[v], w >> 16);
+        mypk[v] = 0u;
+      }
+    }
+    __syncthreads();
+    flush_cta(P, i, hs, lo, cnt, brd, 256);
+    __syncthreads();
+    image_rows_done(P, i, seg, scratch, sh_int, sb, (size_t)P.smem_bytes);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+    __syncthreads();
+    r0 = seg_end;
+    ++i;
+  }
+}
+
+// ----------------------------------------------------------------------------- generic pass
+// Any layout and alignment, uint8 or uint16, M <= bins: one lane per pixel of a
+// 32-pixel strip, walking down rows; three shared-memory updates per pair
+// (H_lo, H_hi, H_s).  With GLOBAL the updates go straight to the image's global
+// histograms (for M too large for shared memory).
+template <int ELEM, bool GLOBAL>
+__global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchParams P) {
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint64_t scratch[40];
+  __shared__ int sh_int[40];
+  constexpr int NW = 8;
+  const int bins = P.bins;
+  uint32_t* hlo = smem;
+  uint32_t* hhi = hlo + bins;
+  uint32_t* hs = hhi + bins;
+  if (!GLOBAL) {
+    for (int k = threadIdx.x; k < 4 * bins; k += blockDim.x) smem[k] = 0u;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t T_all = P.total_rs;
+  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
+  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
+  int i = r0 < r1 ? image_of(P, r0) : 0;
+  while (r0 < r1) {
+    const ImgDesc& d = P.img[i];
+    const int BH = d.y1 - d.y0;
+    const int64_t seg_end = min(r1, d.rs_begin + (int64_t)d.strips * BH);
+    const int64_t seg = seg_end - r0;
+    const int W = d.W, H = d.H;
+    unsigned long long* g = P.hist + (size_t)d.slot * 4 * bins;
+    bool bad = false;
+    int64_t a = r0 + (seg * warp) / NW;
+    const int64_t b = r0 + (seg * (warp + 1)) / NW;
+    while (a < b) {
+      const int64_t q = a - d.rs_begin;
+      const int strip = (int)(q / BH);
+      const int ya = d.y0 + (int)(q % BH);
+      const int yb = (int)min64((int64_t)d.y1, (int64_t)ya + (b - a));
+      a += yb - ya;
+      const int x = strip * 32 + lane;
+      const bool act = x < W;
+      auto px = [&](int yy, int xx) -> uint32_t {
+        const unsigned char* p = d.base + (int64_t)yy * d.pitch + (int64_t)xx * ELEM;
+        return ELEM == 1 ? (uint32_t)p[0] : (uint32_t)(*reinterpret_cast<const uint16_t*>(p));
+      };
+      uint32_t cur = act ? px(ya, x) : 0u;
+      for (int y = ya; y < yb; ++y) {
+        const uint32_t nxt = (act && y + 1 < H) ? px(y + 1, x) : 0u;
+        uint32_t right = __shfl_down_sync(0xffffffffu, cur, 1);
+        if (act && x + 1 < W && lane == 31) right = px(y, x + 1);
+        if (act) {
+          bad |= cur >= (uint32_t)P.M;
+          const uint32_t c = min(cur, (uint32_t)P.M - 1);
+          auto add_pair = [&](uint32_t o) {
+            bad |= o >= (uint32_t)P.M;
+            o = min(o, (uint32_t)P.M - 1);
+            const uint32_t l = min(c, o), h = max(c, o);
+            if (GLOBAL) {
+              atomicAdd(g + l, 1ull);
+              atomicAdd(g + bins + h, 1ull);
+              atomicAdd(g + 2 * bins + l + h, 1ull);
+            } else {
+              atomicAdd(&hlo[l], 1u);
+              atomicAdd(&hhi[h], 1u);
+              atomicAdd(&hs[l + h], 1u);
+            }
+          };
+          if (x + 1 < W) add_pair(right);
+          if (y + 1 < H) add_pair(nxt);
+        }
+        cur = nxt;
+      }
+    }
+    if (bad) atomicOr(P.err + d.slot, kErrRange);
+    __syncthreads();
+    if (!GLOBAL) {
+      for (int k = threadIdx.x; k < bins; k += blockDim.x) {
+        if (hlo[k]) atomicAdd(g + k, (unsigned long long)hlo[k]);
+        if (hhi[k]) atomicAdd(g + bins + k, (unsigned long long)hhi[k]);
+        hlo[k] = 0u;
+        hhi[k] = 0u;
+      }
+      for (int k = threadIdx.x; k < 2 * bins; k += blockDim.x) {
+        if (hs[k]) atomicAdd(g + 2 * bins + k, (unsigned long long)hs[k]);
+        hs[k] = 0u;
+      }
+    }
+    __syncthreads();
+    image_rows_done(P, i, seg, scratch, sh_int, reinterpret_cast<unsigned char*>(smem), (size_t)P.smem_bytes);
+    if (!GLOBAL) {
+      for (int k = threadIdx.x; k < 4 * bins; k += blockDim.x) smem[k] = 0u;
+      __syncthreads();
+    }
+    r0 = seg_end;
+    ++i;
+  }
+}
+
+// ----------------------------------------------------------------------------- standalone thresholds
+struct ThreshParams {
+  const uint64_t* card;
+  const uint64_t* sumc;
+  int32_t M, max_k;
+  int32_t* out_t;
+  int32_t* out_count;
+  int32_t* out_t0;
+  int32_t* cand;
+  int32_t cand_stride;
+  int32_t staged;
+};
+
+// With Q.staged the curves are first copied into dynamic shared memory
+// (2 M uint64 + candidates).
+__global__ void __launch_bounds__(kEpiThreads) k_thresholds(const __grid_constant__ ThreshParams Q) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint64_t scratch[40];
+  __shared__ int sh_int[40];
+  const int i = blockIdx.x;
+  const uint64_t* card = Q.card + (size_t)i * Q.M;
+  const uint64_t* sumc = Q.sumc + (size_t)i * Q.M;
+  int32_t* cand = Q.cand + (size_t)i * Q.cand_stride;
+  if (Q.staged) {
+    uint64_t* c = reinterpret_cast<uint64_t*>(dsm);
+    uint64_t* s = c + Q.M;
+    for (int t = threadIdx.x; t < Q.M; t += blockDim.x) {
+      c[t] = card[t];
+      s[t] = sumc[t];
+    }
+    card = c;
+    sumc = s;
+    cand = reinterpret_cast<int32_t*>(s + Q.M);
+    __syncthreads();
+  }
+  select_thresholds(card, sumc, Q.M, Q.max_k, Q.out_t ? Q.out_t + (size_t)i * Q.max_k : nullptr, Q.out_count + i,
+                    Q.out_t0 + i, cand, sh_int, scratch);
+}
+
+}  // namespace kohler
