@@ -139,7 +139,7 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
 int strip_px(Pass p) {
   switch (p) {
     case Pass::FastU8:
-    case Pass::FastU8Check: return 256;
+    case Pass::FastU8Check: return 32;
     case Pass::FastU16: return 32 * TraitsU16::PX;
     default: return 32;
   }
@@ -154,9 +154,9 @@ struct KernelInfo {
 KernelInfo kernel_for(Pass p, int bins) {
   switch (p) {
     case Pass::FastU8:
-      return {(const void*)k_u8<kFastWarps, false>, kFastWarps * 32, (size_t)(u8::kWords + kFastWarps * 256) * 4};
+      return {(const void*)k_u8t<kFastWarps, false>, kFastWarps * 32, (size_t)u8t::kWords * 4};
     case Pass::FastU8Check:
-      return {(const void*)k_u8<kFastWarps, true>, kFastWarps * 32, (size_t)(u8::kWords + kFastWarps * 256) * 4};
+      return {(const void*)k_u8t<kFastWarps, true>, kFastWarps * 32, (size_t)u8t::kWords * 4};
     case Pass::FastU16:
       return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
     case Pass::GenericU8: return {(const void*)k_generic<1, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
@@ -198,6 +198,9 @@ struct Band {
   int32_t y0, y1;
 };
 
+// Rows per work unit: the uint8 pass works on tiles of 8 rows, the others on rows.
+int unit_rows(Pass p) { return (p == Pass::FastU8 || p == Pass::FastU8Check) ? 8 : 1; }
+
 // Launches the pass over `count` images (all of one Pass) already described in
 // `idx` (indices into imgs); slots = position in the launch.
 int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* imgs, const std::vector<Band>* bands,
@@ -223,8 +226,9 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
     d.slot = slot_of[i];
     d.out = out_index ? out_index[i] : i;
     d.rs_begin = rs;
-    d.pad_ = 0;
-    rs += (int64_t)d.strips * (d.y1 - d.y0);
+    const int ur = unit_rows(pass);
+    d.units_total = (uint32_t)((int64_t)d.strips * ((im.height + ur - 1) / ur));
+    rs += (int64_t)d.strips * ((d.y1 - d.y0 + ur - 1) / ur);
     ++P.n;
   }
   if (P.n == 0) return KOHLER_OK;
@@ -234,9 +238,26 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   KernelInfo k = kernel_for(pass, bins);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
   P.smem_bytes = (int32_t)k.smem;
-  const int grid = grid_for(k, rs);
+  int grid = grid_for(k, rs);
+  if (pass == Pass::FastU8 || pass == Pass::FastU8Check) {
+    // at most u8t::kMaxTilesPerWarp tiles per warp and segment (16-bit packed fields)
+    const int64_t per_block = (int64_t)(k.threads / 32) * (u8t::kMaxTilesPerWarp - 1);
+    grid = (int)std::max<int64_t>(grid, (rs + per_block - 1) / per_block);
+  }
+  // programmatic dependent launch: this pass may start while the previous
+  // kernel on the stream finishes (it waits for it before writing global memory)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(k.threads);
+  cfg.dynamicSmemBytes = k.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   void* args[] = {&P};
-  cudaError_t e = cudaLaunchKernel(k.fn, dim3(grid), dim3(k.threads), args, k.smem, stream);
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k.fn, args);
   return status_of(e);
 }
 
@@ -508,8 +529,10 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   if (rc) return rc;
   char* dimg = static_cast<char*>(h->dimg);
   char* dout = static_cast<char*>(h->dout);
+  // band edges on multiples of 8 rows (the uint8 pass works on 8-row tiles)
   std::vector<int32_t> yb(nbands + 1);
-  for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)((height * b) / nbands);
+  for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)std::min<int64_t>(height, ((height * b) / nbands + 7) / 8 * 8);
+  yb[nbands] = (int32_t)height;
   cudaError_t e = cudaSuccess;
   for (int b = 0; b < nbands && e == cudaSuccess; ++b) {
     const int64_t r0 = yb[b], r1 = yb[b + 1];

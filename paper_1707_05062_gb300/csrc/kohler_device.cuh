@@ -45,7 +45,7 @@ struct ImgDesc {
   int32_t strips;             // column strips of the kernel's strip width
   int32_t slot;               // workspace slot (histograms, counters)
   int32_t out;                // index into the output arrays
-  int32_t pad_;
+  uint32_t units_total;       // work units of the whole image (all bands): completion count
 };
 
 struct LaunchParams {
@@ -85,6 +85,14 @@ __device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long*
 }
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// Programmatic dependent launch.  A pass kernel lets the next kernel of the
+// stream start as soon as all its blocks are running (allow_dependents), and
+// waits for the previous kernel to finish only before its first write to
+// global memory (wait_prior): the pass only reads its images, so it overlaps
+// the previous launch's epilogue.  Both are no-ops without the launch attribute.
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Exact comparison of sumc(a)/card(a) with sumc(b)/card(b) (both cards > 0):
 // sign of sumc(a) * card(b) - sumc(b) * card(a) over 128-bit products.
@@ -354,7 +362,7 @@ __device__ void image_rows_done(const LaunchParams& P, int i, int64_t n, uint64_
   __syncthreads();
   if (threadIdx.x == 0) {
     const ImgDesc& d = P.img[i];
-    const unsigned total = (unsigned)((int64_t)d.strips * d.H);  // all bands of the image
+    const unsigned total = d.units_total;  // all bands of the image
     const unsigned prev = atomicAdd(P.done + d.slot, (unsigned)n);
     sh_int[0] = (prev + (unsigned)n == total) ? 1 : 0;
   }
@@ -373,14 +381,10 @@ __device__ __forceinline__ int image_of(const LaunchParams& P, int64_t r) {
 }
 
 // ----------------------------------------------------------------------------- uint16 pass traits
-// Pixels travel as pairs of 16-bit lanes in 32-bit registers.  For a pair
-// (first -> second), second + BIAS - first has bit log2(BIAS) of each lane set
-// iff second >= first, with no borrow between lanes (values < BIAS).
+// Pixels travel as pairs of 16-bit lanes in 32-bit registers.
 struct TraitsU16 {
   static constexpr int PX = 4;
   static constexpr int NV = 2;
-  static constexpr uint32_t BIAS = 0x10001000u;  // values clamped below 4096
-  static constexpr int SHIFT = 12;
   static constexpr int ELEM = 2;
   static __device__ __forceinline__ void unpack(uint2 raw, uint32_t (&v)[NV]) {
     v[0] = raw.x;
@@ -416,16 +420,17 @@ __device__ __forceinline__ void flush_cta(const LaunchParams& P, int i, uint32_t
 
 // ----------------------------------------------------------------------------- uint16 pass
 // Each warp walks a run of rows of one column strip (32 lanes x PX pixels).
-// Lane registers hold the current row V and the next row N as 16x2 lanes;
-// per row it forms the right pairs (V, R) and the lower pairs (V, N), updates
-// the s histogram once per pair and the pixel count / n_lo bins once per pixel
-// (block-wide 32-bit bins: 4096 values are too many for per-warp copies).
+// Lane registers hold the current row V and the next row N as 16x2 lanes; per
+// row it forms the right pairs (V, R) and the lower pairs (V, N).  With 4096
+// values the bins are too many for per-lane copies, so every update adds 1 (the
+// value the shared-memory unit can merge across lanes): the pixel count at f(p),
+// and per pair its lower end (H_lo directly) and its sum s.  H_hi then follows
+// as 4 * count - border - H_lo, as in the uint8 pass.
 // Requirements (checked on the host): W % PX == 0, base and pitch multiples of 8.
 template <class T, int NW, bool CHECK>
 __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ LaunchParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   constexpr int PX = T::PX, NV = T::NV;
-  constexpr uint32_t BIAS = T::BIAS;
   const int bins = P.bins;
   uint32_t* hs = smem;
   uint32_t* lo = hs + 2 * bins;
@@ -438,6 +443,7 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
   const size_t words = (size_t)bins * 5;
   for (size_t k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
   __syncthreads();
+  allow_dependents();
 
   const uint32_t mclamp = (uint32_t)(P.M - 1) | ((uint32_t)(P.M - 1) << 16);
   const int64_t T_all = P.total_rs;
@@ -467,21 +473,19 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
       const bool act = x0 < W;
       const bool lastlane = act && (x0 + PX == W);
       const bool need_right = act && !lastlane && lane == 31;
-      const bool need_left = act && x0 > 0 && lane == 0;
       const unsigned char* col = d.base + (int64_t)x0 * T::ELEM;
-      // one row of this lane: its PX pixels, plus (lane 31 / lane 0) the pixel just
-      // right / left of the strip, which the neighbouring strip's warp owns
+      // one row of this lane: its PX pixels, plus (lane 31) the pixel just right
+      // of the strip, which the next strip's warp owns
       auto load_row = [&](int yy, uint2& raw, uint32_t& edge) {
         raw = make_uint2(0u, 0u);
         edge = 0u;
         if (act && yy < H) {
           const unsigned char* pr = col + (int64_t)yy * pitch;
           raw = load8<T::ELEM>(pr);
-          if (need_right) edge = (T::ELEM == 1) ? (uint32_t)__ldg(pr + PX) : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(pr + PX * 2));
-          if (need_left) edge = (T::ELEM == 1) ? (uint32_t)__ldg(pr - 1) : (uint32_t)__ldg(reinterpret_cast<const uint16_t*>(pr - 2));
+          if (need_right) edge = __ldg(reinterpret_cast<const uint16_t*>(pr + PX * 2));
         }
       };
-      uint32_t V[NV], N[NV], GEup[NV];
+      uint32_t V[NV], N[NV];
       uint2 rc, pf0, pf1;
       uint32_t ec, ef0, ef1;
       load_row(ya, rc, ec);
@@ -492,21 +496,6 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
 #pragma unroll
         for (int k = 0; k < NV; ++k) { vmax = __vmaxu2(vmax, V[k]); V[k] = __vminu2(V[k], mclamp); }
       }
-      if (ya > 0) {
-        uint2 ru;
-        uint32_t eu;
-        load_row(ya - 1, ru, eu);
-        uint32_t U[NV];
-        T::unpack(ru, U);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-          if (CHECK) U[k] = __vminu2(U[k], mclamp);
-          GEup[k] = (V[k] + BIAS - U[k]) & BIAS;  // pair (upper -> p): flag [f(p) >= f(upper)]
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) GEup[k] = BIAS;  // no upper pair: contributes nothing to n_lo
-      }
       for (int y = ya; y < yb; ++y) {
         const bool has_down = y + 1 < H;
         const uint2 rn = pf0;
@@ -514,44 +503,35 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
         pf0 = pf1;
         ef0 = ef1;
         load_row(y + 3 <= yb ? y + 3 : H, pf1, ef1);  // rows up to yb are needed (lower pairs of row yb - 1)
-        // neighbours across lanes of the current row
-        uint32_t rv = __shfl_down_sync(0xffffffffu, V[0], 1);    // its low lane: right neighbour
-        uint32_t lv = __shfl_up_sync(0xffffffffu, V[NV - 1], 1); // its high lane: left neighbour
+        // right neighbour of the lane's last pixel: the next lane's first pixel
+        uint32_t rv = __shfl_down_sync(0xffffffffu, V[0], 1);
         if (need_right) rv = CHECK ? min(ec, (uint32_t)(P.M - 1)) : ec;
         if (lastlane) rv = V[NV - 1] >> 16;  // no right pair: pad with an equal pair
-        if (lane == 0) {
-          // no left pair: a neighbour of value 0 gives flag 1, i.e. no n_lo
-          lv = need_left ? ((CHECK ? min(ec, (uint32_t)(P.M - 1)) : ec) << 16) : 0u;
-        }
         T::unpack(rn, N);
         if (CHECK) {
 #pragma unroll
           for (int k = 0; k < NV; ++k) { vmax = __vmaxu2(vmax, N[k]); N[k] = __vminu2(N[k], mclamp); }
         }
         if (act) {
-          uint32_t R[NV], GEr[NV], GEd[NV];
+          uint32_t R[NV];
 #pragma unroll
           for (int k = 0; k < NV; ++k) R[k] = prmt(V[k], k + 1 < NV ? V[k + 1] : rv, 0x5432u);
+          // every update adds 1 (the same value in all lanes), which lets the
+          // shared-memory unit merge lanes that hit the same bin
 #pragma unroll
           for (int k = 0; k < NV; ++k) {
-            GEr[k] = (R[k] + BIAS - V[k]) & BIAS;                    // pairs (p -> right)
-            GEd[k] = has_down ? ((N[k] + BIAS - V[k]) & BIAS) : 0u;  // pairs (p -> lower)
-          }
-#pragma unroll
-          for (int k = 0; k < NV; ++k) {
-            const uint32_t GEl = (k == 0) ? ((V[0] + BIAS - prmt(lv, V[0], 0x5432u)) & BIAS)
-                                          : prmt(GEr[k - 1], GEr[k], 0x5432u);
-            // n_lo(p) = [right >= p] + [lower >= p] + [left > p] + [upper > p], x BIAS
-            const uint32_t nlo = (GEr[k] + GEd[k] + 2u * BIAS) - (GEl + GEup[k]);
-            const uint32_t p0 = V[k] & 0xffffu, p1 = V[k] >> 16;
-            atomicAdd(&cnt[p0], 1u);
-            atomicAdd(&lo[p0], (nlo >> T::SHIFT) & 0xfu);
-            atomicAdd(&cnt[p1], 1u);
-            atomicAdd(&lo[p1], nlo >> (16 + T::SHIFT));
+            atomicAdd(&cnt[V[k] & 0xffffu], 1u);
+            atomicAdd(&cnt[V[k] >> 16], 1u);
+            const uint32_t lr = __vminu2(V[k], R[k]);  // lower ends of the right pairs
+            atomicAdd(&lo[lr & 0xffffu], 1u);
+            atomicAdd(&lo[lr >> 16], 1u);
             const uint32_t sr = V[k] + R[k];
             atomicAdd(&hs[sr & 0xffffu], 1u);
             atomicAdd(&hs[sr >> 16], 1u);
             if (has_down) {
+              const uint32_t ld = __vminu2(V[k], N[k]);  // lower ends of the lower pairs
+              atomicAdd(&lo[ld & 0xffffu], 1u);
+              atomicAdd(&lo[ld >> 16], 1u);
               const uint32_t sd = V[k] + N[k];
               atomicAdd(&hs[sd & 0xffffu], 1u);
               atomicAdd(&hs[sd >> 16], 1u);
@@ -570,14 +550,12 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
           if (x0 == 0) atomicAdd(&brd[V[0] & 0xffffu], 1);
           if (lastlane) atomicAdd(&brd[V[NV - 1] >> 16], -1);
 #pragma unroll
-          for (int k = 0; k < NV; ++k) {
-            GEup[k] = GEd[k];
-            V[k] = N[k];
-          }
+          for (int k = 0; k < NV; ++k) V[k] = N[k];
         }
         ec = en;
       }
     }
+    wait_prior();
     if (CHECK && ((vmax & 0xffffu) >= (uint32_t)P.M || (vmax >> 16) >= (uint32_t)P.M)) atomicOr(P.err + d.slot, kErrRange);
     __syncthreads();
     flush_cta(P, i, hs, lo, cnt, brd, bins);
@@ -850,6 +828,255 @@ __global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchPa
   }
 }
 
+// ----------------------------------------------------------------------------- uint8 tile pass
+// Same arithmetic as k_u8, with two changes for the shared-memory atomic unit.
+// (1) A warp is laid over a tile of 32 columns x 8 rows: lane l holds the 8
+// pixels x = xs + 8 (l & 3) .. + 7 of row y = ty + (l >> 2), so the 32 keys of
+// one update come from a compact 32 x 8 patch and fall into few distinct values.
+// Vertical neighbours come from the lane 4 positions away (a lower row of the
+// tile, or, for the tile's last row, the next tile's first row that lane (c, 0)
+// has already prefetched); the flags of the upper pairs come from the lane above
+// (for the first row: from lane (c, 7) of the previous tile).  A warp walks down
+// a 32-column strip.
+// (2) Updates that add the same value in every lane merge lanes that hit the
+// same word, so the pair-sum bins (which add 1) need one copy; the packed
+// per-pixel bins add different values, and there each of the 32 lanes adds into
+// its own copy (word v * 32 + lane: the bank is the lane), shared by the warps of
+// the block.  The copies are folded at the end of each image segment; the grid
+// is sized so that a warp reduces at most kMaxTilesPerWarp tiles of a segment,
+// which keeps the 16-bit fields of a copy below 2^16.
+// Work unit: one tile (32 x 8).  Requirements as for k_u8.
+namespace u8t {
+constexpr int kCopies = 32;
+constexpr int kPkWords = 256 * kCopies;        // per-lane copies of the packed pixel bins
+constexpr int kWords = kPkWords + 512 + 3 * 256; // + hs[512], lo[256], cnt[256], brd[256]
+constexpr int kMaxTilesPerWarp = 60;           // 8 warps * 60 tiles * 8 px * 16 < 2^16
+}  // namespace u8t
+
+template <int NW, bool CHECK>
+__global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchParams P) {
+  using namespace u8;
+  extern __shared__ __align__(16) uint32_t smem[];
+  __shared__ uint64_t scratch[40];
+  __shared__ int sh_int[40];
+  unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
+  uint32_t* const pk = smem;                                  // [256][32]
+  uint32_t* const hs = smem + u8t::kPkWords;                  // [512]
+  uint32_t* const lo = hs + 512;
+  uint32_t* const cnt = lo + 256;
+  int32_t* const brd = reinterpret_cast<int32_t*>(cnt + 256);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int c = lane & 3, r = lane >> 2;
+  const int words = u8t::kWords;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  // 16-bit shared addresses in each lane of a key register: pixel bin of value v
+  // at sbase + 128 v + 4 lane, pair-sum bin of s at hs + 4 s
+  const uint32_t pk_addr = sbase + 4u * (uint32_t)lane;
+  const uint32_t PK2 = pk_addr | (pk_addr << 16);
+  const uint32_t hs_addr = sbase + 4u * (uint32_t)u8t::kPkWords;
+  const uint32_t HS2 = hs_addr | (hs_addr << 16);
+  if (hs_addr + 4u * 512u >= 65536u) {  // shared addresses are block-relative and small
+    if (threadIdx.x == 0) atomicOr(P.sticky, kErrInternal);
+    return;
+  }
+  for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+  __syncthreads();
+  allow_dependents();
+  const uint32_t clamp4 = CHECK ? (uint32_t)(4 * (P.M - 1)) * 0x00010001u : 0u;
+  const uint32_t lastv4 = (uint32_t)(4 * (P.M - 1));
+  const int src_dn = (lane + 4) & 31, src_up = (lane + 28) & 31;
+
+  const int64_t T_all = P.total_rs;
+  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
+  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
+  int i = r0 < r1 ? image_of(P, r0) : 0;
+  while (r0 < r1) {
+    const ImgDesc& d = P.img[i];
+    const int tiles = (d.y1 - d.y0 + 7) >> 3;
+    const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * tiles);
+    const int64_t seg = seg_end - r0;
+    const int W = d.W, H = d.H;
+    const int64_t pitch = d.pitch;
+    uint32_t vmax = 0;
+    int64_t a = r0 + (seg * warp) / NW;
+    const int64_t b = r0 + (seg * (warp + 1)) / NW;
+    while (a < b) {
+      const int64_t q = a - d.rs_begin;
+      const int strip = (int)(q / tiles);
+      const int ta = (int)(q % tiles);
+      const int tb = (int)min64((int64_t)tiles, (int64_t)ta + (b - a));
+      a += tb - ta;
+      const int x0 = strip * 32 + c * 8;
+      const bool act = x0 < W;
+      const bool lastcol = act && (x0 + 8 == W);
+      const bool need_right = act && !lastcol && c == 3;
+      const bool need_left = act && x0 > 0 && c == 0;
+      const bool edge_strip = (strip == 0) || ((strip + 1) * 32 >= W);
+      const int ys = d.y0 + 8 * ta;          // first row of the run (tile row 0)
+      // Loads never branch: a row past the image reads the last row, a lane past
+      // the image width reads the row's last 8 pixels, a lane without a strip-edge
+      // pixel reads its own first pixel; none of these is ever reduced.
+      const unsigned char* colp = d.base + (act ? x0 : W - 8);
+      const int eoff = need_right ? 8 : (need_left ? -1 : 0);
+      int y = ys + r;                        // this lane's row in the current tile
+      auto ld = [&](int yy, uint2& raw, uint32_t& edge4) {
+        const unsigned char* p = colp + (int64_t)min(yy, H - 1) * pitch;
+        raw = __ldg(reinterpret_cast<const uint2*>(p));
+        const uint32_t e = __ldg(p + eoff);
+        edge4 = CHECK ? min(e << 2, lastv4) : e << 2;
+      };
+      auto clampv = [&](Row& v) {
+        if (CHECK) {
+          v.E0 = __vminu2(v.E0, clamp4); v.O0 = __vminu2(v.O0, clamp4);
+          v.E1 = __vminu2(v.E1, clamp4); v.O1 = __vminu2(v.O1, clamp4);
+        }
+      };
+      uint2 rc, pf0, pf1;
+      uint32_t ec, ef0, ef1;
+      ld(y, rc, ec);
+      ld(y + 8, pf0, ef0);
+      ld(y + 16, pf1, ef1);
+      Row V = unpack(rc);
+      if (CHECK) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V.E0, V.O0)), __vmaxu2(V.E1, V.O1));
+      clampv(V);
+      // flags of the pairs (row ys - 1 -> row ys) for lane (c, 0), handed to
+      // lane (c, 7) as if it had computed them for a previous tile
+      uint32_t DpE0, DpO0, DpE1, DpO1;
+      {
+        uint2 ru;
+        uint32_t eu;
+        ld(ys - 1 + (ys == 0), ru, eu);
+        Row U = unpack(ru);
+        clampv(U);
+        uint32_t fE0 = B, fO0 = B, fE1 = B, fO1 = B;
+        if (ys > 0) { fE0 = ge(V.E0, U.E0); fO0 = ge(V.O0, U.O0); fE1 = ge(V.E1, U.E1); fO1 = ge(V.O1, U.O1); }
+        DpE0 = __shfl_sync(0xffffffffu, fE0, src_dn);  // lane (c, 7) takes lane (c, 0)'s flags
+        DpO0 = __shfl_sync(0xffffffffu, fO0, src_dn);
+        DpE1 = __shfl_sync(0xffffffffu, fE1, src_dn);
+        DpO1 = __shfl_sync(0xffffffffu, fO1, src_dn);
+      }
+      for (int t = ta; t < tb; ++t) {
+        const uint2 rn = pf0;
+        const uint32_t en = ef0;
+        pf0 = pf1;
+        ef0 = ef1;
+        ld(y + 24, pf1, ef1);
+        // this lane's row of the next tile, and the lower row: from lane (c, r + 1),
+        // or for r = 7 from lane (c, 0)'s row of the next tile
+        Row Vn = unpack(rn);
+        if (CHECK) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(Vn.E0, Vn.O0)), __vmaxu2(Vn.E1, Vn.O1));
+        clampv(Vn);
+        Row N;
+        N.E0 = __shfl_sync(0xffffffffu, r == 0 ? Vn.E0 : V.E0, src_dn);
+        N.O0 = __shfl_sync(0xffffffffu, r == 0 ? Vn.O0 : V.O0, src_dn);
+        N.E1 = __shfl_sync(0xffffffffu, r == 0 ? Vn.E1 : V.E1, src_dn);
+        N.O1 = __shfl_sync(0xffffffffu, r == 0 ? Vn.O1 : V.O1, src_dn);
+        const bool proc = act && y < d.y1;   // rows of this band only
+        const bool has_down = y + 1 < H;
+        // right neighbour of p7
+        uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
+        if (need_right) nb = ec;
+        if (lastcol) nb = V.O1 >> 16;
+        const uint32_t E0s = prmt(V.E0, V.E1, 0x5432u);  // (p2, p4)
+        const uint32_t E1s = prmt(V.E1, nb, 0x5432u);    // (p6, p8)
+        const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
+        uint32_t DE0 = 0, DO0 = 0, DE1 = 0, DO1 = 0;
+        if (has_down) { DE0 = ge(N.E0, V.E0); DO0 = ge(N.O0, V.O0); DE1 = ge(N.E1, V.E1); DO1 = ge(N.O1, V.O1); }
+        // upper pairs: flags computed by the lane above (lane (c, 7) offers its previous tile's)
+        const uint32_t UE0 = __shfl_sync(0xffffffffu, r == 7 ? DpE0 : DE0, src_up);
+        const uint32_t UO0 = __shfl_sync(0xffffffffu, r == 7 ? DpO0 : DO0, src_up);
+        const uint32_t UE1 = __shfl_sync(0xffffffffu, r == 7 ? DpE1 : DE1, src_up);
+        const uint32_t UO1 = __shfl_sync(0xffffffffu, r == 7 ? DpO1 : DO1, src_up);
+        DpE0 = DE0; DpO0 = DO0; DpE1 = DE1; DpO1 = DO1;
+        // pair (p-1 -> p0)
+        uint32_t gl = __shfl_up_sync(0xffffffffu, GO1, 1);
+        if (c == 0) {
+          const uint32_t el4 = need_left ? ec : 0u;
+          gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
+        }
+        const uint32_t LE0 = prmt(gl, GO0, 0x5432u);
+        const uint32_t LE1 = prmt(GO0, GO1, 0x5432u);
+        const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
+        const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
+        const uint32_t nE1 = (GE1 + DE1 + 2 * B) - (LE1 + UE1);
+        const uint32_t nO1 = (GO1 + DO1 + 2 * B) - (GE1 + UO1);
+        if (proc) {
+          const uint32_t aE0 = (V.E0 << 5) + PK2, aO0 = (V.O0 << 5) + PK2;
+          const uint32_t aE1 = (V.E1 << 5) + PK2, aO1 = (V.O1 << 5) + PK2;
+          red_s(aE0 & 0xffffu, prmt(nE0, 0x00010000u, 0x7601u));
+          red_s(aE0 >> 16, prmt(nE0, 0x00010000u, 0x7603u));
+          red_s(aO0 & 0xffffu, prmt(nO0, 0x00010000u, 0x7601u));
+          red_s(aO0 >> 16, prmt(nO0, 0x00010000u, 0x7603u));
+          red_s(aE1 & 0xffffu, prmt(nE1, 0x00010000u, 0x7601u));
+          red_s(aE1 >> 16, prmt(nE1, 0x00010000u, 0x7603u));
+          red_s(aO1 & 0xffffu, prmt(nO1, 0x00010000u, 0x7601u));
+          red_s(aO1 >> 16, prmt(nO1, 0x00010000u, 0x7603u));
+          const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
+          const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
+          red_s(sE0 & 0xffffu, 1u);
+          red_s(sE0 >> 16, 1u);
+          red_s(sO0 & 0xffffu, 1u);
+          red_s(sO0 >> 16, 1u);
+          red_s(sE1 & 0xffffu, 1u);
+          red_s(sE1 >> 16, 1u);
+          red_s(sO1 & 0xffffu, 1u);
+          red_s(sO1 >> 16, 1u);
+          if (has_down) {
+            const uint32_t dE0 = V.E0 + N.E0 + HS2, dO0 = V.O0 + N.O0 + HS2;
+            const uint32_t dE1 = V.E1 + N.E1 + HS2, dO1 = V.O1 + N.O1 + HS2;
+            red_s(dE0 & 0xffffu, 1u);
+            red_s(dE0 >> 16, 1u);
+            red_s(dO0 & 0xffffu, 1u);
+            red_s(dO0 >> 16, 1u);
+            red_s(dE1 & 0xffffu, 1u);
+            red_s(dE1 >> 16, 1u);
+            red_s(dO1 & 0xffffu, 1u);
+            red_s(dO1 >> 16, 1u);
+          }
+          if (y == 0 || !has_down) {
+            const int rowb = (y == 0 ? 1 : 0) + (has_down ? 0 : 1);
+            const uint32_t vv[4] = {V.E0, V.O0, V.E1, V.O1};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              atomicAdd(&brd[(vv[k] & 0xffffu) >> 2], rowb);
+              atomicAdd(&brd[vv[k] >> 18], rowb);
+            }
+          }
+          if (edge_strip) {
+            if (x0 == 0) atomicAdd(&brd[(V.E0 & 0xffffu) >> 2], 1);
+            if (lastcol) atomicAdd(&brd[V.O1 >> 18], -1);
+          }
+        }
+        V = Vn;
+        ec = en;
+        y += 8;
+      }
+    }
+    wait_prior();
+    if (CHECK && ((vmax & 0xffffu) > lastv4 || (vmax >> 16) > lastv4)) atomicOr(P.err + d.slot, kErrRange);
+    __syncthreads();
+    // fold the 32 copies of each pixel bin: warp w takes bins w, w + NW, ...
+    for (int v = warp; v < 256; v += NW) {
+      const uint32_t w = pk[v * 32 + lane];
+      pk[v * 32 + lane] = 0u;
+      const uint32_t l4 = __reduce_add_sync(0xffffffffu, w & 0xffffu);
+      const uint32_t n = __reduce_add_sync(0xffffffffu, w >> 16);
+      if (lane == 0) {
+        lo[v] += l4 >> 2;
+        cnt[v] += n;
+      }
+    }
+    __syncthreads();
+    flush_cta(P, i, hs, lo, cnt, brd, 256);
+    __syncthreads();
+    image_rows_done(P, i, seg, scratch, sh_int, sb, (size_t)P.smem_bytes);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+    __syncthreads();
+    r0 = seg_end;
+    ++i;
+  }
+}
+
 // ----------------------------------------------------------------------------- generic pass
 // Any layout and alignment, uint8 or uint16, M <= bins: one lane per pixel of a
 // 32-pixel strip, walking down rows; three shared-memory updates per pair
@@ -869,6 +1096,8 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchP
     for (int k = threadIdx.x; k < 4 * bins; k += blockDim.x) smem[k] = 0u;
     __syncthreads();
   }
+  allow_dependents();
+  if (GLOBAL) wait_prior();  // this variant writes global histograms during the pass
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t T_all = P.total_rs;
   int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
@@ -924,6 +1153,7 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchP
         cur = nxt;
       }
     }
+    wait_prior();
     if (bad) atomicOr(P.err + d.slot, kErrRange);
     __syncthreads();
     if (!GLOBAL) {
