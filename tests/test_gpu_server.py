@@ -1,0 +1,184 @@
+"""The continuous-batching frame server (kohler_submit / kohler_poll).
+
+Every frame's thresholds must be the same whether it is served alone or mixed
+with other frames that arrive while it is on the GPU (tolerance zero: the
+results are exact integers), and equal to the oracle's.
+"""
+import ctypes
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(300)]
+MAX_K = 8
+
+
+@pytest.fixture(scope="module")
+def K():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_05062_gb300 import build
+
+    build.build()
+    oracle.build()
+    import paper_1707_05062_gb300 as k
+
+    return k
+
+
+class Server:
+    def __init__(self, K, M=256, budget=0, inflight=0):
+        self.K = K
+        self.L = K.lib()
+        self.h = ctypes.c_void_p()
+        assert self.L.kohler_server_create(ctypes.byref(self.h), M, MAX_K, budget, inflight) == 0
+
+    def submit(self, frame):
+        t = ctypes.c_uint64()
+        code = 1 if frame.dtype == np.uint8 else 2
+        rc = self.L.kohler_submit(self.h, frame.ctypes.data, code, frame.shape[1], frame.shape[0], frame.strides[0],
+                                  ctypes.byref(t))
+        return rc, t.value
+
+    def poll(self, ticket, timeout_us=-1):
+        ts = (ctypes.c_int32 * MAX_K)()
+        res = self.K.KohlerResult()
+        res.thresholds = ctypes.cast(ts, ctypes.c_void_p)
+        rc = self.L.kohler_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(res), timeout_us)
+        return rc, res.t0, res.count, list(ts), res.latency_s
+
+    def stats(self):
+        v = [ctypes.c_uint64() for _ in range(4)]
+        assert self.L.kohler_server_stats(self.h, *[ctypes.byref(x) for x in v]) == 0
+        return [x.value for x in v]
+
+    def close(self):
+        assert self.L.kohler_server_destroy(self.h) == 0
+
+
+def expected(frame, M=256):
+    card, sumc = oracle.curve_alg1(frame, M)
+    ts, cnt, t0 = oracle.thresholds(card, sumc, MAX_K)
+    return t0, cnt, ts.tolist()
+
+
+def frames(n, seed=0):
+    scene = synth.VideoScene(seed=77 + seed)
+    sizes = [(640, 480), (1920, 1080), (320, 240), (1280, 720), (64, 48), (100, 37)]
+    return [scene.frame(k, *sizes[k % len(sizes)]) for k in range(n)]
+
+
+def test_alone_and_mixed(K):
+    fr = frames(12)
+    want = [expected(f) for f in fr]
+    s = Server(K)
+    try:
+        alone = []
+        for f in fr:  # one frame in flight at a time
+            rc, t = s.submit(f)
+            assert rc == 0
+            rc, t0, cnt, ts, lat = s.poll(t)
+            assert rc == 0 and lat > 0
+            alone.append((t0, cnt, ts))
+        # all frames at once from two producer threads: launches batch what is resident
+        tickets = [None] * len(fr)
+
+        def produce(idx):
+            for i in idx:
+                rc, t = s.submit(fr[i])
+                assert rc == 0
+                tickets[i] = t
+
+        th = [threading.Thread(target=produce, args=(range(j, len(fr), 2),)) for j in range(2)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        mixed = []
+        for t in tickets:
+            rc, t0, cnt, ts, lat = s.poll(t)
+            assert rc == 0
+            mixed.append((t0, cnt, ts))
+        assert alone == mixed == want
+        sub, fin, launches, maxb = s.stats()
+        assert sub == fin == 2 * len(fr)
+        assert launches <= 2 * len(fr)
+    finally:
+        s.close()
+
+
+def test_pending_timeout_unknown_and_curve(K):
+    s = Server(K)
+    try:
+        f = frames(1)[0]
+        rc, t = s.submit(f)
+        assert rc == 0
+        rc0 = s.poll(t, timeout_us=0)[0]
+        assert rc0 in (K.OK, K.PENDING)
+        if rc0 == K.PENDING:
+            # wait for completion, then fetch the device curve before releasing the ticket
+            deadline = time.time() + 30
+            while time.time() < deadline:
+                dc = ctypes.c_void_p()
+                r = s.L.kohler_server_curve(s.h, ctypes.c_uint64(t), ctypes.byref(dc))
+                if r == K.OK:
+                    break
+                time.sleep(0.001)
+            assert r == K.OK and dc.value
+            rc, t0, cnt, ts, lat = s.poll(t, timeout_us=1000000)
+            assert rc == 0
+            assert (t0, cnt, ts) == expected(f)
+        assert s.poll(987654321, timeout_us=0)[0] == K.ERR_ARG  # unknown ticket
+    finally:
+        s.close()
+
+
+def test_range_error_frame(K):
+    s = Server(K, M=100)
+    try:
+        bad = synth.smooth_image(3, 64, 32, 100)
+        bad[5, 5] = 200
+        good = synth.smooth_image(4, 64, 32, 100)
+        rb, tb = s.submit(bad)
+        rg, tg = s.submit(good)
+        assert rb == 0 and rg == 0
+        assert s.poll(tb)[0] == K.ERR_RANGE
+        rc, t0, cnt, ts, lat = s.poll(tg)
+        assert rc == 0
+        card, sumc = oracle.curve_alg1(good, 100)
+        ots, ocnt, ot0 = oracle.thresholds(card, sumc, MAX_K)
+        assert (t0, cnt, ts) == (ot0, ocnt, ots.tolist())
+    finally:
+        s.close()
+
+
+def test_memory_budget_admission(K):
+    # a budget that holds one 1920x1080 frame at a time: frames wait for memory, none is lost
+    s = Server(K, budget=1920 * 1080 + 1024, inflight=4)
+    try:
+        scene = synth.VideoScene(seed=9)
+        fr = [scene.frame(k, 1920, 1080) for k in range(4)]
+        tickets = [s.submit(f)[1] for f in fr]
+        for f, t in zip(fr, tickets):
+            rc, t0, cnt, ts, lat = s.poll(t)
+            assert rc == 0 and (t0, cnt, ts) == expected(f)
+        # a frame larger than the whole budget can never be admitted
+        big = synth.VideoScene(seed=10).frame(0, 3840, 2160)
+        rc, t = s.submit(big)
+        assert rc == 0
+        assert s.poll(t, timeout_us=10_000_000)[0] == K.ERR_NOMEM
+    finally:
+        s.close()
+
+
+def test_destroy_with_frames_in_flight(K):
+    s = Server(K)
+    for f in frames(6, seed=3):
+        assert s.submit(f)[0] == 0
+    s.close()  # drains admitted frames, drops queued ones, returns
