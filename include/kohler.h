@@ -116,6 +116,23 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
                         int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc,
                         double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0);
 
+/* kohler_analyze_batch for one device image, without any device allocation (the
+ * paper has no counterpart; this serves callers that cannot allocate while they
+ * run, e.g. inside a real-time loop or under a fixed memory budget).  Scratch
+ * lives in a fixed 144 KiB array in device memory that every GPU which loads the
+ * library keeps until the process exits; M is limited to 4096 (KOHLER_ERR_ARG
+ * above).  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress): make that first call before capturing the stream
+ * into a CUDA graph.  Each call clears the array on `cuda_stream` before use.
+ * All calls share the one array, so calls whose work overlaps on the GPU
+ * (different streams, or two host threads) race; serialize them.
+ * out_status: device int32[1], KOHLER_OK or KOHLER_ERR_RANGE (pixel >= M, outputs
+ * all zero); other outputs as in kohler_analyze_batch for n = 1. */
+int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
+                           int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve,
+                           int32_t* out_t, int32_t* out_count, int32_t* out_t0, int32_t* out_status,
+                           void* cuda_stream);
+
 /* Waits for `cuda_stream` and returns the deferred status of the calls enqueued
  * on it since the previous kohler_stream_status: KOHLER_ERR_RANGE if an image had
  * a pixel >= M, KOHLER_ERR_CUDA on a CUDA error, else KOHLER_OK. */

@@ -63,6 +63,9 @@ def lib():
             L.kohler_analyze_batch.argtypes = [p, i32, i, i32, i, i32, p, p, p, p, p, p, p]
             L.kohler_analyze_host.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p]
             L.kohler_stream_status.argtypes = [p]
+            if hasattr(L, "kohler_analyze_noalloc"):
+                L.kohler_analyze_noalloc.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p, p, p]
+                L.kohler_analyze_noalloc.restype = i
             L.kohler_release.argtypes = []
             L.kohler_strerror.argtypes = [i]
             L.kohler_strerror.restype = ctypes.c_char_p

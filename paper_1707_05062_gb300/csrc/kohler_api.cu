@@ -572,3 +572,89 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- allocation-free entry point
+// For callers that may not allocate device memory while they run: code inside
+// a real-time loop that must not stall in the allocator, allocator-less
+// runtimes, or processes whose memory budget is fixed up front.  Everything the
+// pass and its epilogue need beyond the caller's buffers lives in one
+// fixed-size array that every device holds from module load until the process
+// exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 144 * 1024;
+constexpr int kNoAllocMaxM = 4096;  // 4 bins * 4096 * 8 B of histograms + candidates fit
+
+// Laid out as: histograms (4 * bins uint64), then at kCountersAt the image's
+// completion counter, error bits and the sticky error word, then at kCandAt the
+// threshold candidates.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr size_t kCountersAt = (size_t)4 * kNoAllocMaxM * 8;      // 131072
+constexpr size_t kCandAt = kCountersAt + 256;
+static_assert(kCandAt + ((size_t)(kNoAllocMaxM + 1) / 2 + 2) * 4 <= kNoAllocScratchBytes, "scratch too small");
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal (set up once)
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  if (dev < 0 || dev >= 64) return KOHLER_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    // the host-side symbol is a stand-in, not a device address: ask the runtime
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return e != cudaSuccess ? status_of(e) : KOHLER_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KOHLER_OK;
+}
+
+}  // namespace
+
+extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int64_t height,
+                                      int64_t pitch_bytes, int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card,
+                                      uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count,
+                                      int32_t* out_t0, int32_t* out_status, void* cuda_stream) {
+  int rc = check_common(dt, M, nb);
+  if (rc) return rc;
+  if (M > kNoAllocMaxM) return KOHLER_ERR_ARG;  // histograms would not fit the fixed scratch
+  rc = check_image(img, dt, width, height, pitch_bytes);
+  if (rc) return rc;
+  if (!card || !sumc || max_k < 0 || (max_k > 0 && !out_t) || !out_count || !out_t0 || !out_status)
+    return KOHLER_ERR_ARG;
+  void* scratch = nullptr;
+  rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  const kohler_image im{img, width, height, pitch_bytes};
+  const Pass pass = pass_for(im, dt, M);
+  if (pass == Pass::GlobalU8 || pass == Pass::GlobalU16) return KOHLER_ERR_ARG;
+  const int bins = bins_for(dt, M);
+  char* s = static_cast<char*>(scratch);
+  // the array keeps the previous call's contents: clear histograms and counters
+  cudaError_t e = cudaMemsetAsync(s, 0, kCandAt, stream);
+  if (e != cudaSuccess) return status_of(e);
+  LaunchParams base;
+  memset(&base, 0, sizeof(base));
+  base.M = M;
+  base.max_k = max_k;
+  base.card = card;
+  base.sumc = sumc;
+  base.curve = curve;
+  base.out_t = max_k > 0 ? out_t : nullptr;
+  base.out_count = out_count;
+  base.out_t0 = out_t0;
+  base.out_status = out_status;
+  base.hist = reinterpret_cast<unsigned long long*>(s);
+  base.done = reinterpret_cast<unsigned*>(s + kCountersAt);
+  base.err = reinterpret_cast<unsigned*>(s + kCountersAt + 4);
+  base.sticky = reinterpret_cast<unsigned*>(s + kCountersAt + 8);
+  base.cand = reinterpret_cast<int32_t*>(s + kCandAt);
+  base.cand_stride = (M + 1) / 2 + 2;
+  std::vector<int> idx(1, 0), slot_of(1, 0);
+  return launch_group(pass, idx, &im, nullptr, M, bins, nullptr, base, stream, slot_of, nullptr);
+}
