@@ -190,7 +190,11 @@ int grid_for(const KernelInfo& k, int64_t total_rs) {
     per_sm = 1;
   const int64_t warps = k.threads / 32;
   int64_t want = (total_rs + warps * kRowsPerWarp - 1) / (warps * kRowsPerWarp);
-  want = std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sms * per_sm));
+  // one block short of a full wave: the previous launch's last block may still
+  // run its epilogue on one slot when this launch starts (programmatic launch),
+  // and a block waiting for that slot would finish last
+  const int64_t slots = (int64_t)sms * per_sm;
+  want = std::max<int64_t>(1, std::min<int64_t>(want, slots > 1 ? slots - 1 : 1));
   return (int)want;
 }
 

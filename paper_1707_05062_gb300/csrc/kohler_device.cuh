@@ -74,9 +74,11 @@ struct LaunchParams {
 };
 
 // ----------------------------------------------------------------------------- small helpers
-__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+// Byte permute with a compile-time selector (an immediate operand).
+template <uint32_t SEL>
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b) {
   uint32_t r;
-  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(sel));
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "n"(SEL));
   return r;
 }
 
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
         if (act) {
           uint32_t R[NV];
 #pragma unroll
-          for (int k = 0; k < NV; ++k) R[k] = prmt(V[k], k + 1 < NV ? V[k + 1] : rv, 0x5432u);
+          for (int k = 0; k < NV; ++k) R[k] = prmt<0x5432u>(V[k], k + 1 < NV ? V[k + 1] : rv);
           // every update adds 1 (the same value in all lanes), which lets the
           // shared-memory unit merge lanes that hit the same bin
 #pragma unroll
@@ -714,8 +716,8 @@ __global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchPa
         uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
         if (need_right) nb = CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2;
         if (lastlane) nb = V.O1 >> 16;
-        const uint32_t E0s = prmt(V.E0, V.E1, 0x5432u);  // (p2, p4)
-        const uint32_t E1s = prmt(V.E1, nb, 0x5432u);    // (p6, p8)
+        const uint32_t E0s = prmt<0x5432u>(V.E0, V.E1);  // (p2, p4)
+        const uint32_t E1s = prmt<0x5432u>(V.E1, nb);    // (p6, p8)
         // flags [second >= first] of the right pairs, per register of first pixels
         const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
         // lower pairs
@@ -728,8 +730,8 @@ __global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchPa
           const uint32_t el4 = need_left ? (CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2) : 0u;
           gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
         }
-        const uint32_t LE0 = prmt(gl, GO0, 0x5432u);   // pairs ending at p0, p2
-        const uint32_t LE1 = prmt(GO0, GO1, 0x5432u);  // pairs ending at p4, p6
+        const uint32_t LE0 = prmt<0x5432u>(gl, GO0);   // pairs ending at p0, p2
+        const uint32_t LE1 = prmt<0x5432u>(GO0, GO1);  // pairs ending at p4, p6
         // n_lo * 1024 per pixel: [right >= p] + [lower >= p] + [left > p] + [upper > p]
         const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
         const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
@@ -738,14 +740,14 @@ __global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchPa
         if (act) {
           // per-pixel packed bins: payload (4 n_lo) | (1 << 16)
           const uint32_t aE0 = V.E0 + PK2, aO0 = V.O0 + PK2, aE1 = V.E1 + PK2, aO1 = V.O1 + PK2;
-          red_s(aE0 & 0xffffu, prmt(nE0, 0x00010000u, 0x7601u));
-          red_s(aE0 >> 16, prmt(nE0, 0x00010000u, 0x7603u));
-          red_s(aO0 & 0xffffu, prmt(nO0, 0x00010000u, 0x7601u));
-          red_s(aO0 >> 16, prmt(nO0, 0x00010000u, 0x7603u));
-          red_s(aE1 & 0xffffu, prmt(nE1, 0x00010000u, 0x7601u));
-          red_s(aE1 >> 16, prmt(nE1, 0x00010000u, 0x7603u));
-          red_s(aO1 & 0xffffu, prmt(nO1, 0x00010000u, 0x7601u));
-          red_s(aO1 >> 16, prmt(nO1, 0x00010000u, 0x7603u));
+          red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, 0x00010000u));
+          red_s(aE0 >> 16, prmt<0x7603u>(nE0, 0x00010000u));
+          red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, 0x00010000u));
+          red_s(aO0 >> 16, prmt<0x7603u>(nO0, 0x00010000u));
+          red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, 0x00010000u));
+          red_s(aE1 >> 16, prmt<0x7603u>(nE1, 0x00010000u));
+          red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, 0x00010000u));
+          red_s(aO1 >> 16, prmt<0x7603u>(nO1, 0x00010000u));
           // pair sums s = f(p) + f(q): shared addresses of hs[s]
           const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
           const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
@@ -854,7 +856,7 @@ constexpr int kMaxTilesPerWarp = 60;           // 8 warps * 60 tiles * 8 px * 16
 }  // namespace u8t
 
 template <int NW, bool CHECK>
-__global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchParams P) {
+__global__ void __launch_bounds__(NW * 32, (NW == 8 ? 4 : 1)) k_u8t(const __grid_constant__ LaunchParams P) {
   using namespace u8;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[40];
@@ -901,9 +903,9 @@ __global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchP
     int64_t a = r0 + (seg * warp) / NW;
     const int64_t b = r0 + (seg * (warp + 1)) / NW;
     while (a < b) {
-      const int64_t q = a - d.rs_begin;
-      const int strip = (int)(q / tiles);
-      const int ta = (int)(q % tiles);
+      const uint32_t q = (uint32_t)(a - d.rs_begin);  // < 2^32 units per image (checked on the host)
+      const int strip = (int)(q / (uint32_t)tiles);
+      const int ta = (int)(q - (uint32_t)strip * (uint32_t)tiles);
       const int tb = (int)min64((int64_t)tiles, (int64_t)ta + (b - a));
       a += tb - ta;
       const int x0 = strip * 32 + c * 8;
@@ -977,8 +979,8 @@ __global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchP
         uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
         if (need_right) nb = ec;
         if (lastcol) nb = V.O1 >> 16;
-        const uint32_t E0s = prmt(V.E0, V.E1, 0x5432u);  // (p2, p4)
-        const uint32_t E1s = prmt(V.E1, nb, 0x5432u);    // (p6, p8)
+        const uint32_t E0s = prmt<0x5432u>(V.E0, V.E1);  // (p2, p4)
+        const uint32_t E1s = prmt<0x5432u>(V.E1, nb);    // (p6, p8)
         const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
         uint32_t DE0 = 0, DO0 = 0, DE1 = 0, DO1 = 0;
         if (has_down) { DE0 = ge(N.E0, V.E0); DO0 = ge(N.O0, V.O0); DE1 = ge(N.E1, V.E1); DO1 = ge(N.O1, V.O1); }
@@ -994,8 +996,8 @@ __global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchP
           const uint32_t el4 = need_left ? ec : 0u;
           gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
         }
-        const uint32_t LE0 = prmt(gl, GO0, 0x5432u);
-        const uint32_t LE1 = prmt(GO0, GO1, 0x5432u);
+        const uint32_t LE0 = prmt<0x5432u>(gl, GO0);
+        const uint32_t LE1 = prmt<0x5432u>(GO0, GO1);
         const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
         const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
         const uint32_t nE1 = (GE1 + DE1 + 2 * B) - (LE1 + UE1);
@@ -1003,14 +1005,14 @@ __global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchP
         if (proc) {
           const uint32_t aE0 = (V.E0 << 5) + PK2, aO0 = (V.O0 << 5) + PK2;
           const uint32_t aE1 = (V.E1 << 5) + PK2, aO1 = (V.O1 << 5) + PK2;
-          red_s(aE0 & 0xffffu, prmt(nE0, 0x00010000u, 0x7601u));
-          red_s(aE0 >> 16, prmt(nE0, 0x00010000u, 0x7603u));
-          red_s(aO0 & 0xffffu, prmt(nO0, 0x00010000u, 0x7601u));
-          red_s(aO0 >> 16, prmt(nO0, 0x00010000u, 0x7603u));
-          red_s(aE1 & 0xffffu, prmt(nE1, 0x00010000u, 0x7601u));
-          red_s(aE1 >> 16, prmt(nE1, 0x00010000u, 0x7603u));
-          red_s(aO1 & 0xffffu, prmt(nO1, 0x00010000u, 0x7601u));
-          red_s(aO1 >> 16, prmt(nO1, 0x00010000u, 0x7603u));
+          red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, 0x00010000u));
+          red_s(aE0 >> 16, prmt<0x7603u>(nE0, 0x00010000u));
+          red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, 0x00010000u));
+          red_s(aO0 >> 16, prmt<0x7603u>(nO0, 0x00010000u));
+          red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, 0x00010000u));
+          red_s(aE1 >> 16, prmt<0x7603u>(nE1, 0x00010000u));
+          red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, 0x00010000u));
+          red_s(aO1 >> 16, prmt<0x7603u>(nO1, 0x00010000u));
           const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
           const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
           red_s(sE0 & 0xffffu, 1u);
@@ -1070,10 +1072,12 @@ __global__ void __launch_bounds__(NW * 32) k_u8t(const __grid_constant__ LaunchP
     flush_cta(P, i, hs, lo, cnt, brd, 256);
     __syncthreads();
     image_rows_done(P, i, seg, scratch, sh_int, sb, (size_t)P.smem_bytes);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
-    __syncthreads();
     r0 = seg_end;
     ++i;
+    if (r0 < r1) {  // another image follows: the epilogue may have used the bins as scratch
+      for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
+      __syncthreads();
+    }
   }
 }
 
