@@ -14,6 +14,14 @@ own images (replicas: weak scaling, no data-path collective); rank 0 prints the
 line with the whole-job throughput, timed as the slowest rank.
 `--impl reference` times the CPU oracle (the definitional per-threshold loop) on
 the host cores instead.
+
+At N = 1 the same line carries "forms": the batched form (one launch over a
+96-image uint8 batch, and over 16 uint16 12-bit images with M = 4096) timed
+against one launch per image on the same resident images, and the served form
+(2000 Poisson-arriving video frames of mixed resolution through the
+continuous-batching server: p50/p99 latency, closed-loop frames/s, and one
+synchronous host call per frame for comparison).  Every form checks its
+results against the oracle.
 """
 from __future__ import annotations
 
@@ -286,6 +294,9 @@ def bench_ours(args, rank, local, world, dist):
     traffic = kernel_traffic("k_u8t", "voronoi_18mp")
     e2e = bench_e2e(args, pool_np, M, rank, dist) if not args.no_e2e else None
     cpu = cpu_baseline(pool_np[0], M) if (rank == 0 and world == 1 and not args.no_cpu) else None
+    del pool
+    torch.cuda.empty_cache()
+    forms = run_forms(args, K, torch, dev, peak) if (world == 1 and args.forms) else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": elapsed * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -305,6 +316,8 @@ def bench_ours(args, rank, local, world, dist):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if forms is not None:
+        line["forms"] = forms
     return line
 
 
@@ -336,6 +349,283 @@ def bench_e2e(args, pool_np, M, rank, dist):
     return {"value": total / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(px),
             "d2h_bytes_per_step": int(M * 8 * 3 + MAX_K * 4 + 8), "steps": steps,
             "call": "kohler_analyze_host (pinned host image -> host curve and thresholds)"}
+
+
+# ----------------------------------------------------------------------------- batched and served forms
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _graph_of(torch, dev, fn):
+    """Captures fn(stream) into a CUDA graph on a side stream (after two eager
+    calls there, which create the library's workspace for that stream)."""
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        fn(s)
+        fn(s)
+    torch.cuda.synchronize(dev)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        fn(s)
+    torch.cuda.synchronize(dev)
+    return g, s
+
+
+def _time_graph(torch, g, s, reps):
+    a, b = _events(torch)
+    with torch.cuda.stream(s):
+        g.replay()
+        a.record(s)
+        for _ in range(reps):
+            g.replay()
+        b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def _time_host(torch, fn, s, reps):
+    a, b = _events(torch)
+    fn(s)
+    a.record(s)
+    for _ in range(reps):
+        fn(s)
+    b.record(s)
+    b.synchronize()
+    return a.elapsed_time(b) / 1e3 / reps
+
+
+def form_batched(K, torch, dev, imgs_np, M, name, check_idx, peak):
+    """One launch over the whole batch (per-image histogram slices, per-image
+    epilogues) against one launch per image, on the same device-resident images."""
+    import oracle
+
+    n = len(imgs_np)
+    imgs = [torch.from_numpy(im).to(dev) for im in imgs_np]
+    px = sum(im.size for im in imgs_np)
+    nbytes = sum(im.nbytes for im in imgs_np)
+    outs = alloc_outputs(torch, dev, n, M)
+    rows = [tuple(t[j:j + 1] for t in outs) for j in range(n)]
+
+    def batched(s):
+        K.analyze_batch(imgs, M, MAX_K, out=outs, stream=s)
+
+    def plain(s):
+        for j in range(n):
+            K.analyze_batch([imgs[j]], M, MAX_K, out=rows[j], stream=s)
+
+    res = {"images": n, "mpixel": px / 1e6, "bytes": nbytes, "M": M}
+    gb, sb = _graph_of(torch, dev, batched)
+    t1 = _time_graph(torch, gb, sb, 2)
+    reps = int(min(200, max(5, 0.5 / max(t1, 1e-6))))
+    tb = _time_graph(torch, gb, sb, reps)
+    tb_host = _time_host(torch, batched, sb, reps)
+    if K.stream_status(sb) != K.OK:
+        raise RuntimeError(f"{name}: batched launch reported an error")
+    gp, sp = _graph_of(torch, dev, plain)
+    tp = _time_graph(torch, gp, sp, max(3, reps // 4))
+    tp_host = _time_host(torch, plain, sp, max(3, reps // 4))
+    if K.stream_status(sp) != K.OK:
+        raise RuntimeError(f"{name}: per-image launches reported an error")
+    res["batched"] = {"launches_per_step": (n + 127) // 128, "ms_graph": tb * 1e3, "gpx_s_graph": px / tb / 1e9,
+                      "hbm_frac_graph": nbytes / tb / 1e9 / peak, "ms_host": tb_host * 1e3,
+                      "gpx_s_host": px / tb_host / 1e9, "reps": reps}
+    res["plain"] = {"launches_per_step": n, "ms_graph": tp * 1e3, "gpx_s_graph": px / tp / 1e9,
+                    "hbm_frac_graph": nbytes / tp / 1e9 / peak, "ms_host": tp_host * 1e3,
+                    "gpx_s_host": px / tp_host / 1e9}
+    res["batched_over_plain_graph"] = tp / tb
+    res["batched_over_plain_host"] = tp_host / tb_host
+    # parity of sampled images of the batch (outputs of the last plain replay
+    # and of a fresh batched call must both equal the oracle)
+    batched(torch.cuda.current_stream(dev))
+    torch.cuda.synchronize(dev)
+    ok = True
+    for j in check_idx:
+        ocard, osumc, oc, ots, ocnt, ot0 = oracle.analyze(imgs_np[j], M, MAX_K, method="alg1")
+        ok = ok and bool(np.array_equal(outs[0][j].cpu().numpy().view(np.uint64), ocard)
+                         and np.array_equal(outs[1][j].cpu().numpy().view(np.uint64), osumc)
+                         and np.array_equal(outs[2][j].cpu().numpy(), oc)
+                         and np.array_equal(outs[3][j].cpu().numpy(), ots)
+                         and int(outs[4][j]) == ocnt and int(outs[5][j]) == ot0)
+    res["parity_spot_check"] = {"images": list(check_idx), "equal": ok}
+    del imgs, outs, rows, gb, gp
+    torch.cuda.empty_cache()
+    return res
+
+
+class _Server:
+    def __init__(self, K, M, max_k):
+        import ctypes
+
+        self.K, self.L, self.ct = K, K.lib(), ctypes
+        self.h = ctypes.c_void_p()
+        self.max_k = max_k
+        rc = self.L.kohler_server_create(ctypes.byref(self.h), M, max_k, 0, 0)
+        if rc != 0:
+            raise RuntimeError(f"kohler_server_create: {rc}")
+
+    def submit(self, frame):
+        ct = self.ct
+        t = ct.c_uint64()
+        while True:
+            rc = self.L.kohler_submit(self.h, frame.ctypes.data, 1, frame.shape[1], frame.shape[0], frame.strides[0],
+                                      ct.byref(t))
+            if rc != self.K.ERR_BUSY:
+                break
+            time.sleep(0.0002)
+        if rc != 0:
+            raise RuntimeError(f"kohler_submit: {rc}")
+        return t.value
+
+    def poll(self, ticket):
+        ct = self.ct
+        ts = (ct.c_int32 * max(1, self.max_k))()
+        res = self.K.KohlerResult()
+        res.thresholds = ct.cast(ts, ct.c_void_p)
+        rc = self.L.kohler_poll(self.h, ct.c_uint64(ticket), ct.byref(res), -1)
+        if rc != 0:
+            raise RuntimeError(f"kohler_poll: {rc}")
+        return res.t0, res.count, list(ts)[:self.max_k], res.latency_s
+
+    def stats(self):
+        ct = self.ct
+        v = [ct.c_uint64() for _ in range(4)]
+        self.L.kohler_server_stats(self.h, *[ct.byref(x) for x in v])
+        return [x.value for x in v]
+
+    def close(self):
+        self.L.kohler_server_destroy(self.h)
+
+
+def _pct(xs, q):
+    return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
+
+
+def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_frames=600, plain_frames=300):
+    """Poisson-arriving video frames of mixed resolutions through the server
+    (continuous batching), against one synchronous host call per frame."""
+    import queue
+
+    import oracle
+    import synth
+
+    arrivals, res_idx = synth.video_schedule(n_frames, fps)
+    scene = synth.VideoScene()
+    # `distinct` rendered frames per resolution, cycled in arrival order
+    frames = {r: [scene.frame(k, *synth.VIDEO_SIZES[r]) for k in range(distinct)] for r in range(len(synth.VIDEO_SIZES))}
+    src = []
+    seen = [0] * len(synth.VIDEO_SIZES)
+    for r in res_idx:
+        src.append((int(r), seen[r] % distinct))
+        seen[r] += 1
+    want = {}
+    for r, fl in frames.items():
+        for k, f in enumerate(fl):
+            card, sumc = oracle.curve_alg1(f, 256)
+            ts, cnt, t0 = oracle.thresholds(card, sumc, MAX_K)
+            want[(r, k)] = (int(t0), int(cnt), ts.tolist())
+    px = np.array([frames[r][k].size for r, k in src], dtype=np.float64)
+    out = {"frames": n_frames, "fps_offered": fps, "mean_mpixel_per_frame": float(px.mean() / 1e6),
+           "resolutions": {f"{w}x{h}": int((res_idx == r).sum()) for r, (w, h) in enumerate(synth.VIDEO_SIZES)},
+           "content": f"{distinct} rendered frames per resolution, cycled in arrival order"}
+
+    def run(order, times):
+        srv = _Server(K, 256, MAX_K)
+        q = queue.Queue()
+        results = [None] * len(order)
+        t_base = time.perf_counter() + 0.05
+
+        def producer():
+            for j, (r, k) in enumerate(order):
+                if times is not None:
+                    dt = t_base + times[j] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                t_arr = t_base + times[j] if times is not None else time.perf_counter()
+                q.put((j, srv.submit(frames[r][k]), t_arr))
+
+        th = threading.Thread(target=producer)
+        t_start = time.perf_counter()
+        th.start()
+        for _ in range(len(order)):
+            j, ticket, t_arr = q.get()
+            t0, cnt, ts, lat_srv = srv.poll(ticket)
+            results[j] = (t0, cnt, ts, time.perf_counter() - t_arr, lat_srv)
+        th.join()
+        t_end = time.perf_counter()
+        stats = srv.stats()
+        srv.close()
+        return results, (t_start if times is None else t_base), t_end, stats
+
+    ok = True
+    # (i) open loop: Poisson arrivals at `fps`
+    results, t_a, t_b, stats = run(src, arrivals)
+    lat = [r[3] for r in results]
+    ok = ok and all((r[0], r[1], r[2]) == want[s] for r, s in zip(results, src))
+    out["open_loop"] = {"fps_achieved": n_frames / (t_b - t_a), "latency_ms_p50": _pct(lat, 50) * 1e3,
+                        "latency_ms_p99": _pct(lat, 99) * 1e3, "latency_ms_max": max(lat) * 1e3,
+                        "server_latency_ms_p50": _pct([r[4] for r in results], 50) * 1e3,
+                        "server_latency_ms_p99": _pct([r[4] for r in results], 99) * 1e3,
+                        "launches": stats[2], "max_frames_per_launch": stats[3],
+                        "latency": "scheduled arrival -> thresholds in host memory"}
+    # (ii) closed loop: every frame submitted as soon as the staging queue takes it
+    sub = src[:closed_frames]
+    results, t_a, t_b, stats = run(sub, None)
+    ok = ok and all((r[0], r[1], r[2]) == want[s] for r, s in zip(results, sub))
+    lat = [r[3] for r in results]
+    out["closed_loop"] = {"frames": len(sub), "fps": len(sub) / (t_b - t_a),
+                          "gpx_s": float(px[:len(sub)].sum()) / (t_b - t_a) / 1e9,
+                          "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
+                          "launches": stats[2], "max_frames_per_launch": stats[3]}
+    # (iii) plain: one synchronous host call per frame (pinned frames), in arrival order
+    pinned = {key: torch.from_numpy(frames[key[0]][key[1]]).pin_memory() for key in want}
+    sub = src[:plain_frames]
+    lat = []
+    t_a = time.perf_counter()
+    for key in sub:
+        t = time.perf_counter()
+        card, sumc, c, ts, cnt, t0 = K.analyze_host(pinned[key], 256, MAX_K)
+        lat.append(time.perf_counter() - t)
+        ok = ok and (t0, cnt, ts.tolist()) == want[key]
+    t_b = time.perf_counter()
+    out["plain_per_frame"] = {"frames": len(sub), "fps": len(sub) / (t_b - t_a),
+                              "gpx_s": float(px[:len(sub)].sum()) / (t_b - t_a) / 1e9,
+                              "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
+                              "call": "kohler_analyze_host per frame"}
+    out["parity_all_frames"] = ok
+    return out
+
+
+def run_forms(args, K, torch, dev, peak):
+    forms = {}
+    names = [x for x in args.forms.split(",") if x]
+    for name in names:
+        t = time.perf_counter()
+        try:
+            if name == "batch96":
+                import synth
+
+                specs = synth.batch96_specs()
+                imgs = synth.voronoi_batch(specs, workers=os.cpu_count() or 1)
+                small = min(range(len(imgs)), key=lambda j: imgs[j].size)
+                large = max(range(len(imgs)), key=lambda j: imgs[j].size)
+                forms[name] = form_batched(K, torch, dev, imgs, 256, name, (small, large), peak)
+                forms[name]["workload"] = "96 Voronoi uint8 images, sizes 320x240 .. 4096x3072, M = 256"
+            elif name == "cosine_u16_batch16":
+                import synth
+
+                imgs = synth.cosine_u16_batch()
+                forms[name] = form_batched(K, torch, dev, imgs, 4096, name, (), peak)
+                forms[name]["workload"] = "16 uint16 2048x2048 12-bit cosine fields, M = 4096"
+                forms[name]["parity_spot_check"]["note"] = "full-size parity: tests/test_gpu_parity.py (slow mark)"
+            elif name == "served":
+                forms[name] = form_served(K, torch, dev)
+            else:
+                forms[name] = {"error": "unknown form"}
+        except Exception as e:  # a failing form is reported, not hidden
+            forms[name] = {"error": f"{type(e).__name__}: {e}"}
+        forms[name]["wall_s"] = time.perf_counter() - t
+    return forms
 
 
 def bench_reference(args, rank, world):
@@ -383,6 +673,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served",
+                    help="comma list of extra forms reported in the same line (N = 1 only); empty for none")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -84,7 +84,7 @@ int kohler_curve(const void* img, kohler_dtype dt, int64_t width, int64_t height
                  void* cuda_stream);
 
 /* Contrast curves of n images with one dtype and M, in one launch (or one per
- * 64 images).  imgs: HOST array of n descriptors (read before the call returns).
+ * 128 images).  imgs: HOST array of n descriptors (read before the call returns).
  * card, sumc: device uint64[n][M]; curve: device double[n][M] (may be NULL). */
 int kohler_curve_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
                        uint64_t* card, uint64_t* sumc, double* curve, void* cuda_stream);

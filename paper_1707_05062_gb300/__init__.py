@@ -166,7 +166,7 @@ def thresholds(card: torch.Tensor, sumc: torch.Tensor, max_k: int, *, stream=Non
 
 def analyze_batch(imgs: Sequence[torch.Tensor], M: int, max_k: int, *, with_curve: bool = True, stream=None,
                   out=None):
-    """Fused curves and thresholds of n device images (one launch per 64 images).
+    """Fused curves and thresholds of n device images (one launch per 128 images).
     Returns (card, sumc, curve, out_t, count, t0); `out` may supply these tensors."""
     n = len(imgs)
     dev = imgs[0].device

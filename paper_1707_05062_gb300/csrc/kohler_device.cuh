@@ -31,7 +31,7 @@
 
 namespace kohler {
 
-constexpr int kMaxBatch = 64;       // images per launch (descriptors travel in kernel parameters)
+constexpr int kMaxBatch = 128;      // images per launch (descriptors travel in kernel parameters, ~7 KB)
 constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
 
 enum ErrBits : unsigned { kErrRange = 1u, kErrInternal = 2u };
@@ -374,12 +374,16 @@ __device__ void image_rows_done(const LaunchParams& P, int i, int64_t n, uint64_
   if (last) finish_image(P, i, scratch, sh_int, dsm, dsm_bytes);
 }
 
-// Image containing global row-strip r (linear search; n <= kMaxBatch).  Images
-// with an empty band hold no row-strip and are skipped by the search.
+// Image containing global row-strip r: the last image whose first row-strip is
+// <= r (binary search over the n <= kMaxBatch descriptors, whose rs_begin never
+// decreases).  Images with an empty band hold no row-strip and are skipped.
 __device__ __forceinline__ int image_of(const LaunchParams& P, int64_t r) {
-  int i = 0;
-  while (i + 1 < P.n && P.img[i + 1].rs_begin <= r) ++i;
-  return i;
+  int lo = 0, hi = P.n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (P.img[mid].rs_begin <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
 // ----------------------------------------------------------------------------- uint16 pass traits

@@ -149,8 +149,21 @@ def batch96_specs(seed: int = SEEDS["voronoi_batch96"], n: int = 96):
     return out
 
 
-def voronoi_batch(specs) -> list:
-    return [voronoi_image(s, w, h, ns, sd) for (w, h, ns, sd, s) in specs]
+def _voronoi_spec(spec):
+    w, h, ns, sd, s = spec
+    return voronoi_image(s, w, h, ns, sd)
+
+
+def voronoi_batch(specs, workers: int = 1) -> list:
+    """Images of `specs` (see batch96_specs); workers > 1 renders them in a pool
+    of spawned processes (safe after CUDA is initialised), same bytes."""
+    if workers <= 1 or len(specs) < 2:
+        return [_voronoi_spec(sp) for sp in specs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+
+    with ProcessPoolExecutor(max_workers=min(workers, len(specs)), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_voronoi_spec, specs))
 
 
 # ---------------------------------------------------------------- 12-bit cosine fields
@@ -194,17 +207,25 @@ class VideoScene:
 
     def frame(self, k: int, w: int, h: int, noise_sd: float = 5.0) -> np.ndarray:
         g = rng(self.seed * 7919 + 1 + k)
-        yy, xx = np.mgrid[0:h, 0:w].astype(np.float32)
-        xn, yn = xx / w, yy / h
+        xn = (np.arange(w, dtype=np.float32) / np.float32(w))[None, :]
+        yn = (np.arange(h, dtype=np.float32) / np.float32(h))[:, None]
         a = self.bg_rate * k
         f = self.bg0 + self.bg_amp * (np.cos(a) * xn + np.sin(a) * yn)
         for i in range(len(self.level)):
             cx, cy = (self.c[i] + k * self.v[i]) % 1.0
             ct, st = np.cos(self.theta[i]), np.sin(self.theta[i])
-            dx, dy = xn - cx, (yn - cy) * (h / w)
+            # only pixels within the larger semi-axis of the centre can be inside
+            rx = self.ax[i].max()
+            x_a, x_b = max(0, int(np.floor((cx - rx) * w)) - 1), min(w, int(np.ceil((cx + rx) * w)) + 2)
+            y_a = max(0, int(np.floor((cy - rx * w / h) * h)) - 1)
+            y_b = min(h, int(np.ceil((cy + rx * w / h) * h)) + 2)
+            if x_a >= x_b or y_a >= y_b:
+                continue
+            dx, dy = xn[:, x_a:x_b] - cx, (yn[y_a:y_b] - cy) * (h / w)
             u = (dx * ct + dy * st) / self.ax[i, 0]
             v = (-dx * st + dy * ct) / self.ax[i, 1]
-            f = np.where(u * u + v * v <= 1.0, np.float32(self.level[i]), f)
+            sub = f[y_a:y_b, x_a:x_b]
+            f[y_a:y_b, x_a:x_b] = np.where(u * u + v * v <= 1.0, np.float32(self.level[i]), sub)
         f = f + g.normal(0.0, noise_sd, size=(h, w)).astype(np.float32)
         return _to_dtype(f, 255, np.uint8)
 

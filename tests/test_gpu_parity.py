@@ -5,6 +5,8 @@ both sides take the IEEE round-to-nearest quotient of the same two integers),
 and the ranked thresholds, their count and t0 equal exactly.  All calls go
 through the C ABI (the ctypes binding only marshals arguments).
 """
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -245,8 +247,9 @@ def test_batch_mixed_sizes_and_paths():
         assert_same(got2[j], want[p], f"perm {j}")
 
 
-def test_batch_more_than_64():
-    imgs = [synth.smooth_image(500 + i, 40 + 8 * (i % 5), 9 + i % 7, 256) for i in range(70)]
+def test_batch_more_than_one_launch():
+    # 130 images: two launches of at most 128 descriptors
+    imgs = [synth.smooth_image(500 + i, 40 + 8 * (i % 5), 9 + i % 7, 256) for i in range(130)]
     got = run_analyze([to_dev(im) for im in imgs], 256)
     for i, im in enumerate(imgs):
         assert_same(got[i], expect(im, 256), f"image {i}")
@@ -320,7 +323,7 @@ def test_voronoi_18mp_full():
 @pytest.mark.slow
 def test_voronoi_batch96_full():
     specs = synth.batch96_specs()
-    imgs = synth.voronoi_batch(specs)
+    imgs = synth.voronoi_batch(specs, workers=os.cpu_count() or 1)
     got = run_analyze([to_dev(im) for im in imgs], 256)
     for i, im in enumerate(imgs):
         assert_same(got[i], expect(im, 256), f"image {i} {im.shape}")
