@@ -512,7 +512,10 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
     arrivals, res_idx = synth.video_schedule(n_frames, fps)
     scene = synth.VideoScene()
     # `distinct` rendered frames per resolution, cycled in arrival order
-    frames = {r: [scene.frame(k, *synth.VIDEO_SIZES[r]) for k in range(distinct)] for r in range(len(synth.VIDEO_SIZES))}
+    # frames sit in pinned host memory (numpy views of pinned tensors), as a
+    # capture pipeline would deliver them
+    frames = {r: [torch.from_numpy(scene.frame(k, *synth.VIDEO_SIZES[r])).pin_memory().numpy() for k in range(distinct)]
+              for r in range(len(synth.VIDEO_SIZES))}
     src = []
     seen = [0] * len(synth.VIDEO_SIZES)
     for r in res_idx:
@@ -527,7 +530,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
     px = np.array([frames[r][k].size for r, k in src], dtype=np.float64)
     out = {"frames": n_frames, "fps_offered": fps, "mean_mpixel_per_frame": float(px.mean() / 1e6),
            "resolutions": {f"{w}x{h}": int((res_idx == r).sum()) for r, (w, h) in enumerate(synth.VIDEO_SIZES)},
-           "content": f"{distinct} rendered frames per resolution, cycled in arrival order"}
+           "content": f"{distinct} rendered frames per resolution, cycled in arrival order, in pinned host memory"}
 
     def run(order, times):
         srv = _Server(K, 256, MAX_K)
@@ -578,7 +581,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
                           "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
                           "launches": stats[2], "max_frames_per_launch": stats[3]}
     # (iii) plain: one synchronous host call per frame (pinned frames), in arrival order
-    pinned = {key: torch.from_numpy(frames[key[0]][key[1]]).pin_memory() for key in want}
+    pinned = {key: torch.from_numpy(frames[key[0]][key[1]]) for key in want}
     sub = src[:plain_frames]
     lat = []
     t_a = time.perf_counter()

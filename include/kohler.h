@@ -171,8 +171,11 @@ typedef struct {
 int kohler_server_create(kohler_server** s, int32_t M, int32_t max_k, size_t device_mem_budget,
                          int32_t max_inflight);
 
-/* Copies the frame (row-major, pitch_bytes) into pinned staging and queues it;
- * the caller may reuse `host_frame` as soon as the call returns.  *ticket
+/* Takes a copy of the frame (row-major, pitch_bytes) and queues it; the caller
+ * may reuse `host_frame` as soon as the call returns.  When no earlier frame is
+ * waiting and a slot and device memory are free, the frame is copied straight
+ * into its device buffer before the call returns (fastest from pinned memory);
+ * otherwise it is copied into pinned staging and admitted later.  *ticket
  * identifies the frame.  KOHLER_ERR_BUSY when the staging queue is full. */
 int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                   int64_t pitch_bytes, uint64_t* ticket);

@@ -59,6 +59,9 @@ struct kohler_server {
   size_t budget = 1ull << 30;
   size_t staging_cap = 1ull << 30;
   cudaStream_t copy = nullptr, compute = nullptr;
+  cudaStream_t direct = nullptr;  // copies made inside kohler_submit (direct admission)
+  cudaEvent_t direct_done = nullptr;
+  std::mutex direct_mu;           // one direct copy at a time
   // outputs per slot
   uint64_t* d_card = nullptr;
   uint64_t* d_sumc = nullptr;
@@ -214,9 +217,9 @@ void kohler_server::run() {
     std::vector<Frame*> ready;
     for (auto it = copying.begin(); it != copying.end() && ready.size() < 64;) {
       Frame* f = *it;
-      if (cudaEventQuery(f->copied) == cudaSuccess) {
+      if (!f->copied || cudaEventQuery(f->copied) == cudaSuccess) {
         ready.push_back(f);
-        put_event(f->copied);
+        if (f->copied) put_event(f->copied);
         f->copied = nullptr;
         it = copying.erase(it);
       } else {
@@ -317,7 +320,7 @@ void kohler_server::run() {
       lk.lock();
     } else {
       cv_work.wait(lk, [&] {
-        return stop || (!queue.empty() && !free_slots.empty());
+        return stop || !copying.empty() || (!queue.empty() && !free_slots.empty());
       });
     }
   }
@@ -341,6 +344,8 @@ int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t d
   };
   chk(cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking));
   chk(cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking));
+  chk(cudaStreamCreateWithFlags(&s->direct, cudaStreamNonBlocking));
+  chk(cudaEventCreateWithFlags(&s->direct_done, cudaEventDisableTiming));
   chk(cudaMalloc(&s->d_card, sizeof(uint64_t) * M * n));
   chk(cudaMalloc(&s->d_sumc, sizeof(uint64_t) * M * n));
   chk(cudaMalloc(&s->d_curve, sizeof(double) * M * n));
@@ -375,29 +380,68 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
   f->H = height;
   f->dpitch = ((width * es + 127) / 128) * 128;
   f->bytes = (size_t)f->dpitch * height;
-  f->staging_bytes = (size_t)width * es * height;
+  f->t_submit = Clock::now();
+  // Direct admission: when no frame waits ahead of this one and a slot and
+  // device memory are free, the frame is copied from the caller's buffer
+  // straight into its device buffer (no staging copy); the call returns once
+  // that copy has completed, so the caller may reuse its buffer.
   {
-    std::lock_guard<std::mutex> lk(s->mu);
+    std::unique_lock<std::mutex> lk(s->mu);
     if (s->stop) {
       delete f;
       return KOHLER_ERR_ARG;
     }
-    f->staging = s->host_alloc(f->staging_bytes);
+    if (s->queue.empty() && !s->free_slots.empty()) {
+      void* d = s->dev_alloc(f->bytes);
+      if (d) {
+        f->dev = d;
+        f->slot = s->free_slots.back();
+        s->free_slots.pop_back();
+        f->state = FrameState::Copying;
+      }
+    }
+    if (!f->dev) {
+      f->staging_bytes = (size_t)width * es * height;
+      f->staging = s->host_alloc(f->staging_bytes);
+      if (!f->staging) {
+        delete f;
+        return KOHLER_ERR_BUSY;
+      }
+    }
   }
-  if (!f->staging) {
-    delete f;
-    return KOHLER_ERR_BUSY;
-  }
-  f->t_submit = Clock::now();
-  // copy into pinned staging (compact rows); the caller keeps its buffer
-  const char* src = static_cast<const char*>(host_frame);
-  char* dst = static_cast<char*>(f->staging);
-  if (pitch_bytes == width * es) {
-    memcpy(dst, src, f->staging_bytes);
+  if (f->dev) {
+    cudaError_t e;
+    {
+      std::lock_guard<std::mutex> dl(s->direct_mu);
+      e = cudaMemcpy2DAsync(f->dev, f->dpitch, host_frame, pitch_bytes, width * es, height, cudaMemcpyHostToDevice,
+                            s->direct);
+      if (e == cudaSuccess) e = cudaEventRecord(s->direct_done, s->direct);
+      if (e == cudaSuccess) e = cudaEventSynchronize(s->direct_done);
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    f->ticket = s->next_ticket++;
+    s->frames[f->ticket] = f;
+    ++s->n_submitted;
+    *ticket = f->ticket;
+    if (e != cudaSuccess) {
+      f->status = status_of(e);
+      f->state = FrameState::Done;
+      s->dev_release(f->dev, f->bytes);
+      f->dev = nullptr;
+      ++s->n_finished;
+      s->cv_done.notify_all();
+      return KOHLER_OK;  // the error is reported by kohler_poll
+    }
+    s->copying.push_back(f);  // copy complete: no event (f->copied stays null)
   } else {
-    for (int64_t y = 0; y < height; ++y) memcpy(dst + y * width * es, src + y * pitch_bytes, width * es);
-  }
-  {
+    // copy into pinned staging (compact rows); the scheduler admits it later
+    const char* src = static_cast<const char*>(host_frame);
+    char* dst = static_cast<char*>(f->staging);
+    if (pitch_bytes == width * es) {
+      memcpy(dst, src, f->staging_bytes);
+    } else {
+      for (int64_t y = 0; y < height; ++y) memcpy(dst + y * width * es, src + y * pitch_bytes, width * es);
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     f->ticket = s->next_ticket++;
     s->frames[f->ticket] = f;
@@ -501,8 +545,11 @@ int kohler_server_destroy(kohler_server* s) {
   cudaFreeHost(s->h_cnt);
   cudaFreeHost(s->h_t0);
   cudaFreeHost(s->h_status);
+  if (s->direct) cudaStreamSynchronize(s->direct);
   if (s->copy) cudaStreamDestroy(s->copy);
   if (s->compute) cudaStreamDestroy(s->compute);
+  if (s->direct) cudaStreamDestroy(s->direct);
+  if (s->direct_done) cudaEventDestroy(s->direct_done);
   delete s;
   return KOHLER_OK;
 }
