@@ -139,7 +139,7 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
 int strip_px(Pass p) {
   switch (p) {
     case Pass::FastU8:
-    case Pass::FastU8Check: return 32;
+    case Pass::FastU8Check: return u8r::kStripPx;
     case Pass::FastU16: return 32 * TraitsU16::PX;
     default: return 32;
   }
@@ -153,10 +153,8 @@ struct KernelInfo {
 
 KernelInfo kernel_for(Pass p, int bins) {
   switch (p) {
-    case Pass::FastU8:
-      return {(const void*)k_u8t<kFastWarps, false>, kFastWarps * 32, (size_t)u8t::kWords * 4};
-    case Pass::FastU8Check:
-      return {(const void*)k_u8t<kFastWarps, true>, kFastWarps * 32, (size_t)u8t::kWords * 4};
+    case Pass::FastU8: return {(const void*)k_u8r<false>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
+    case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16:
       return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
     case Pass::GenericU8: return {(const void*)k_generic<1, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
@@ -179,9 +177,9 @@ size_t epilogue_smem(int M, int bins, size_t pass_smem) {
   return 0;
 }
 
-// Grid size: enough blocks for ~kRowsPerWarp rows per warp, at most one full
+// Grid size: enough blocks for ~units_per_warp work units per warp, at most one full
 // wave of resident blocks.
-int grid_for(const KernelInfo& k, int64_t total_rs) {
+int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -189,7 +187,7 @@ int grid_for(const KernelInfo& k, int64_t total_rs) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int64_t warps = k.threads / 32;
-  int64_t want = (total_rs + warps * kRowsPerWarp - 1) / (warps * kRowsPerWarp);
+  int64_t want = (total_rs + warps * units_per_warp - 1) / (warps * units_per_warp);
   // one block short of a full wave: the previous launch's last block may still
   // run its epilogue on one slot when this launch starts (programmatic launch),
   // and a block waiting for that slot would finish last
@@ -202,8 +200,17 @@ struct Band {
   int32_t y0, y1;
 };
 
-// Rows per work unit: the uint8 pass works on tiles of 8 rows, the others on rows.
-int unit_rows(Pass p) { return (p == Pass::FastU8 || p == Pass::FastU8Check) ? 8 : 1; }
+// Rows per work unit: the uint8 pass works on units of 8 rows of a strip, the
+// others on rows.
+bool is_fast_u8(Pass p) { return p == Pass::FastU8 || p == Pass::FastU8Check; }
+int unit_rows(Pass p) { return is_fast_u8(p) ? u8r::kUnitRows : 1; }
+
+// What an image's completion counter counts to: the uint8 pass reports
+// strip-rows (any band split adds up), the others their work units.
+uint32_t completion_total(Pass p, int64_t strips, int64_t H) {
+  const int64_t ur = unit_rows(p);
+  return (uint32_t)(is_fast_u8(p) ? strips * H : strips * ((H + ur - 1) / ur));
+}
 
 // Launches the pass over `count` images (all of one Pass) already described in
 // `idx` (indices into imgs); slots = position in the launch.
@@ -231,7 +238,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
     d.out = out_index ? out_index[i] : i;
     d.rs_begin = rs;
     const int ur = unit_rows(pass);
-    d.units_total = (uint32_t)((int64_t)d.strips * ((im.height + ur - 1) / ur));
+    d.units_total = completion_total(pass, d.strips, im.height);
     rs += (int64_t)d.strips * ((d.y1 - d.y0 + ur - 1) / ur);
     ++P.n;
   }
@@ -242,12 +249,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   KernelInfo k = kernel_for(pass, bins);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
   P.smem_bytes = (int32_t)k.smem;
-  int grid = grid_for(k, rs);
-  if (pass == Pass::FastU8 || pass == Pass::FastU8Check) {
-    // at most u8t::kMaxTilesPerWarp tiles per warp and segment (16-bit packed fields)
-    const int64_t per_block = (int64_t)(k.threads / 32) * (u8t::kMaxTilesPerWarp - 1);
-    grid = (int)std::max<int64_t>(grid, (rs + per_block - 1) / per_block);
-  }
+  int grid = grid_for(k, rs, is_fast_u8(pass) ? 2 : kRowsPerWarp);
   // programmatic dependent launch: this pass may start while the previous
   // kernel on the stream finishes (it waits for it before writing global memory)
   cudaLaunchConfig_t cfg = {};
