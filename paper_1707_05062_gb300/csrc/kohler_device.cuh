@@ -33,6 +33,7 @@ namespace kohler {
 
 constexpr int kMaxBatch = 128;      // images per launch (descriptors travel in kernel parameters, ~7 KB)
 constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
+constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, warp winners, per-warp top lists
 
 enum ErrBits : unsigned { kErrRange = 1u, kErrInternal = 2u };
 
@@ -288,21 +289,59 @@ __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, in
     if (out_t0) *out_t0 = b;
     if (out_count) *out_count = K;
   }
-  // 3. rank each candidate: number of candidates that come before it
-  for (int i = tid; i < K; i += nt) {
-    const int ti = cand[i];
-    const uint64_t si = sumc[ti], ci = card[ti];
-    int rank = 0;
-    for (int j = 0; j < K && rank < max_k; ++j) {
-      const int tj = cand[j];
-      if (tj == ti) continue;
-      const int c = cmp_ratio(sumc[tj], card[tj], si, ci);
-      if (c > 0 || (c == 0 && tj < ti)) ++rank;
+  // 3. the first max_k candidates in rank order (C descending, then t ascending)
+  if (out_t && max_k > 0 && max_k <= 32) {
+    __syncthreads();  // sh_int[1..] held the warp winners of step 2
+    // each warp keeps a sorted list of its best candidates, lane r holding rank r
+    // (-1: empty); a batch of 32 candidates is first tested against the list's
+    // last entry, and only those that beat it are inserted one by one
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    auto better = [&](int a, int b) {  // candidate a ranks before b (b may be -1)
+      if (b < 0) return true;
+      const int c = cmp_ratio(sumc[a], card[a], sumc[b], card[b]);
+      return c > 0 || (c == 0 && a < b);
+    };
+    int mine = -1;
+    auto insert_batch = [&](int c) {  // c: this lane's candidate t or -1
+      const int last = __shfl_sync(0xffffffffu, mine, max_k - 1);
+      unsigned m = __ballot_sync(0xffffffffu, c >= 0 && better(c, last));
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const int tn = __shfl_sync(0xffffffffu, c, src);
+        const unsigned worse = __ballot_sync(0xffffffffu, lane < max_k && better(tn, mine));
+        if (!worse) continue;
+        const int pos = __ffs(worse) - 1;
+        const int up = __shfl_up_sync(0xffffffffu, mine, 1);
+        if (lane == pos) mine = tn;
+        else if (lane > pos && lane < max_k) mine = up;
+      }
+    };
+    for (int base = warp * 32; base < K; base += nt) insert_batch(base + lane < K ? cand[base + lane] : -1);
+    int* lists = sh_int + 40;  // [nw][32] within the block's kShInts
+    lists[warp * 32 + lane] = mine;
+    __syncthreads();
+    if (warp == 0) {
+      for (int w = 1; w < nw; ++w) insert_batch(lists[w * 32 + lane]);
+      if (lane < max_k) out_t[lane] = mine;  // -1 where fewer than max_k maxima exist
     }
-    if (rank < max_k && out_t) out_t[rank] = ti;
+    __syncthreads();
+  } else if (out_t) {
+    // any max_k: rank of each candidate = number of candidates before it
+    for (int i = tid; i < K; i += nt) {
+      const int ti = cand[i];
+      const uint64_t si = sumc[ti], ci = card[ti];
+      int rank = 0;
+      for (int j = 0; j < K && rank < max_k; ++j) {
+        const int tj = cand[j];
+        if (tj == ti) continue;
+        const int c = cmp_ratio(sumc[tj], card[tj], si, ci);
+        if (c > 0 || (c == 0 && tj < ti)) ++rank;
+      }
+      if (rank < max_k) out_t[rank] = ti;
+    }
+    for (int r = K + tid; r < max_k; r += nt) out_t[r] = -1;
   }
-  for (int r = K + tid; r < max_k; r += nt)
-    if (out_t) out_t[r] = -1;
   __syncthreads();
 }
 
@@ -443,7 +482,7 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
   uint32_t* cnt = lo + bins;
   int32_t* brd = reinterpret_cast<int32_t*>(cnt + bins);
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const size_t words = (size_t)bins * 5;
@@ -619,7 +658,7 @@ __global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchPa
   using namespace u8;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
   unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
   uint32_t* const hs = smem;        // byte offset 0
   uint32_t* const lo = smem + 512;  // 2048
@@ -864,7 +903,7 @@ __global__ void __launch_bounds__(NW * 32, (NW == 8 ? 4 : 1)) k_u8t(const __grid
   using namespace u8;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
   unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
   uint32_t* const pk = smem;                                  // [256][32]
   uint32_t* const hs = smem + u8t::kPkWords;                  // [512]
@@ -1247,7 +1286,7 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
   constexpr int NW = u8r::kNW;
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
   __shared__ unsigned sh_rows;
   unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
   uint32_t* const pk = smem;                                  // [256][32]
@@ -1447,7 +1486,7 @@ template <int ELEM, bool GLOBAL>
 __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
   constexpr int NW = 8;
   const int bins = P.bins;
   uint32_t* hlo = smem;
@@ -1558,7 +1597,7 @@ struct ThreshParams {
 __global__ void __launch_bounds__(kEpiThreads) k_thresholds(const __grid_constant__ ThreshParams Q) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[40];
+  __shared__ int sh_int[kShInts];
   const int i = blockIdx.x;
   const uint64_t* card = Q.card + (size_t)i * Q.M;
   const uint64_t* sumc = Q.sumc + (size_t)i * Q.M;

@@ -233,6 +233,28 @@ def test_thresholds_exact_ties():
 
 
 # ------------------------------------------------------------------------ batches
+@pytest.mark.parametrize("max_k", [0, 1, 5, 31, 32, 33, 100])
+def test_many_maxima_every_max_k(max_k):
+    # a noisy 12-bit field has hundreds of local maxima: the fused call (top-list
+    # selection for max_k <= 32, ranking otherwise) and the standalone threshold
+    # call must both give the oracle's ranked list, count and t0
+    img = synth.cosine_u16(21, 256, 96)
+    M = 4096
+    card, sumc = oracle.curve_alg1(img, M)
+    ots, ocnt, ot0 = oracle.thresholds(card, sumc, max_k)
+    assert ocnt > 100
+    k = K()
+    out = k.analyze_batch([to_dev(img)], M, max_k)
+    torch.cuda.synchronize()
+    assert np.array_equal(u64(out[0][0]), card) and np.array_equal(u64(out[1][0]), sumc)
+    assert int(out[4][0]) == ocnt and int(out[5][0]) == ot0
+    assert np.array_equal(out[3][0].cpu().numpy()[:max_k], ots)
+    ts, cnt, t0 = k.thresholds(torch.from_numpy(card.view(np.int64)).cuda(), torch.from_numpy(sumc.view(np.int64)).cuda(),
+                               max_k)
+    torch.cuda.synchronize()
+    assert np.array_equal(ts[0].cpu().numpy()[:max_k], ots) and int(cnt[0]) == ocnt and int(t0[0]) == ot0
+
+
 def test_batch_mixed_sizes_and_paths():
     imgs = [synth.smooth_image(100 + i, w, h, 256) for i, (w, h) in
             enumerate([(64, 48), (65, 48), (256, 7), (1, 30), (30, 1), (520, 33), (8, 8), (333, 101)])]
