@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -177,21 +178,47 @@ size_t epilogue_smem(int M, int bins, size_t pass_smem) {
   return 0;
 }
 
+// Resident blocks per SM of a kernel and the device's SM count, computed once per
+// (device, kernel, shared-memory size); the dynamic shared-memory attribute is
+// set at the same time.
+struct Occupancy {
+  int sms = 0, per_sm = 0;
+};
+
+Occupancy occupancy_of(const KernelInfo& k) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void*, size_t>, Occupancy> cache;
+  static std::map<std::pair<int, const void*>, size_t> smem_set;  // largest size set per kernel
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_tuple(dev, k.fn, k.smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  Occupancy o;
+  cudaDeviceGetAttribute(&o.sms, cudaDevAttrMultiProcessorCount, dev);
+  size_t& set = smem_set[std::make_pair(dev, k.fn)];
+  if (k.smem > 48 * 1024 && k.smem > set) {
+    cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
+    set = k.smem;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o.per_sm, k.fn, k.threads, k.smem) != cudaSuccess || o.per_sm < 1)
+    o.per_sm = 1;
+  if (o.sms < 1) o.sms = 1;
+  cache[key] = o;
+  return o;
+}
+
 // Grid size: enough blocks for ~units_per_warp work units per warp, at most one full
 // wave of resident blocks.
 int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp) {
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (k.smem > 48 * 1024) cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k.fn, k.threads, k.smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  const Occupancy o = occupancy_of(k);
   const int64_t warps = k.threads / 32;
   int64_t want = (total_rs + warps * units_per_warp - 1) / (warps * units_per_warp);
   // one block short of a full wave: the previous launch's last block may still
   // run its epilogue on one slot when this launch starts (programmatic launch),
   // and a block waiting for that slot would finish last
-  const int64_t slots = (int64_t)sms * per_sm;
+  const int64_t slots = (int64_t)o.sms * o.per_sm;
   want = std::max<int64_t>(1, std::min<int64_t>(want, slots > 1 ? slots - 1 : 1));
   return (int)want;
 }

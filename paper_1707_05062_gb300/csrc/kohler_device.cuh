@@ -18,9 +18,10 @@
 // The lo/hi histograms are accumulated per PIXEL: pixel p is the lo end of
 // n_lo(p) of its pairs and the hi end of deg(p) - n_lo(p), where deg(p) is its
 // number of in-image 4-neighbours.  So one shared-memory update per pixel
-// (value f(p), payload n_lo(p) and a pixel count) gives H_lo and, with the
-// border deficits, H_hi = 4 * count - border - H_lo.  Only the s histogram
-// needs one update per pair.  Ties (f(p) = f(q)) take the first pixel of the
+// (value f(p), payload n_lo(p) and deg(p)) gives H_lo and H_hi = sum deg - H_lo;
+// the uint16 pass counts pixels instead and subtracts the border deficits,
+// H_hi = 4 * count - border - H_lo.  Only the s histogram needs one update per
+// pair.  Ties (f(p) = f(q)) take the first pixel of the
 // pair as lo, which keeps equal pairs complete in all three histograms.
 //
 // Exactness: all counts are integers; the epilogue works in uint64 (every
@@ -34,6 +35,7 @@ namespace kohler {
 constexpr int kMaxBatch = 128;      // images per launch (descriptors travel in kernel parameters, ~7 KB)
 constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
 constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, warp winners, per-warp top lists
+constexpr int kScratch = 3 * 33;       // shared uint64 scratch of a block (block scans of up to 3 values)
 
 enum ErrBits : unsigned { kErrRange = 1u, kErrInternal = 2u };
 
@@ -107,34 +109,44 @@ __device__ __forceinline__ int cmp_ratio(uint64_t sa, uint64_t ca, uint64_t sb, 
   return 0;
 }
 
-// Block-wide exclusive scan of one uint64 per thread (blockDim.x <= 1024, multiple of 32).
-// `scratch` holds 33 entries.  Returns the exclusive prefix; *total gets the block sum.
-__device__ __forceinline__ uint64_t block_excl_scan(uint64_t v, uint64_t* scratch, uint64_t* total) {
+// Block-wide exclusive scans of N uint64 per thread at once (three barriers for
+// all N).  `scratch` holds 33 N entries.  v[k] is replaced by its exclusive prefix.
+template <int N>
+__device__ __forceinline__ void block_excl_scan_n(uint64_t (&v)[N], uint64_t* scratch) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  uint64_t x = v;
+  uint64_t x[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) x[k] = v[k];
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x[k], o);
+      if (lane >= o) x[k] += y;
+    }
   }
-  if (lane == 31) scratch[warp] = x;
+  if (lane == 31) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) scratch[k * 33 + warp] = x[k];
+  }
   __syncthreads();
   if (warp == 0) {
-    uint64_t w = lane < nw ? scratch[lane] : 0;
-    uint64_t s = w;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint64_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
+    for (int k = 0; k < N; ++k) {
+      const uint64_t w = lane < nw ? scratch[k * 33 + lane] : 0;
+      uint64_t t = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < nw) scratch[k * 33 + lane] = t - w;  // exclusive warp offsets
     }
-    if (lane < nw) scratch[lane] = s - w;  // exclusive warp offsets
-    if (lane == 31) scratch[32] = s;
   }
   __syncthreads();
-  uint64_t r = scratch[warp] + x - v;
-  *total = scratch[32];
+#pragma unroll
+  for (int k = 0; k < N; ++k) v[k] = scratch[k * 33 + warp] + x[k] - v[k];
   __syncthreads();
-  return r;
 }
 
 // ----------------------------------------------------------------------------- epilogue
@@ -150,7 +162,7 @@ __device__ __forceinline__ uint64_t ldh(const unsigned long long* p) {
 // where cumX are inclusive prefix sums.  H_GLOBAL: histograms in global memory
 // (read through L2), else in shared memory.  Writes card and sumc to both
 // (card_o, sumc_o: global outputs; card_s, sumc_s: optional shared copies) and
-// curve (if non-null).  When `bad` the outputs are all zero.
+// curve (if non-null).  When `bad` the outputs are all zero.  One block.
 template <bool H_GLOBAL>
 __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned long long* hhi,
                                const unsigned long long* hs, int M, bool bad, uint64_t* __restrict__ card_o,
@@ -167,10 +179,10 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
     sh += ldh<H_GLOBAL>(hhi + t);
   }
   for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL>(hs + u);
-  uint64_t tot;
-  const uint64_t baseL = block_excl_scan(sl, scratch, &tot);
-  const uint64_t baseH = block_excl_scan(sh, scratch, &tot);
-  const uint64_t baseS = block_excl_scan(ss, scratch, &tot);  // sum of H_s over u < 2 c0
+  uint64_t v3[3] = {sl, sh, ss};
+  block_excl_scan_n<3>(v3, scratch);
+  const uint64_t baseL = v3[0], baseH = v3[1];
+  const uint64_t baseS = v3[2];  // sum of H_s over u < 2 c0
   // pass 2: chunk sums of cumA = cumL + cumH and of g(t) = 2 cumS(2t - 2) + H_s(2t - 1)
   uint64_t sa = 0, sg = 0;
   {
@@ -191,8 +203,10 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
       }
     }
   }
-  const uint64_t baseA = block_excl_scan(sa, scratch, &tot);  // sum of cumA(u) for u < c0
-  const uint64_t baseG = block_excl_scan(sg, scratch, &tot);  // sum of g(u) for u < c0
+  uint64_t v2[2] = {sa, sg};
+  block_excl_scan_n<2>(v2, scratch);
+  const uint64_t baseA = v2[0];  // sum of cumA(u) for u < c0
+  const uint64_t baseG = v2[1];  // sum of g(u) for u < c0
   // pass 3: outputs
   {
     uint64_t cl = baseL, ch = baseH, rlh = baseA, rs = baseG;
@@ -225,118 +239,114 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
 
 // ----------------------------------------------------------------------------- thresholds
 // Local maxima of C(t) = sumc/card among thresholds with card > 0, ranked by C
-// descending then t ascending; t0 = first t with the largest C (Eq. 4).
-// One block.  `cand` is scratch for up to (M + 1) / 2 + 1 candidates.
+// descending then t ascending; t0 = first t with the largest C (Eq. 4).  A
+// local maximum is the first t of a plateau (a maximal run of consecutive valid
+// t with equal C) whose outside neighbours are invalid or strictly lower.  t0 is
+// the first-ranked maximum: the first t reaching the largest C starts a plateau
+// and nothing next to it is higher.
+
+// Whether t starts a plateau that is a local maximum.
+__device__ __forceinline__ bool is_max_start(const uint64_t* card, const uint64_t* sumc, int M, int t) {
+  const uint64_t ct = card[t];
+  if (ct == 0) return false;
+  const uint64_t st = sumc[t];
+  if (t > 0 && card[t - 1] > 0 && cmp_ratio(sumc[t - 1], card[t - 1], st, ct) >= 0) return false;
+  int b = t;
+  while (b + 1 < M && card[b + 1] > 0 && cmp_ratio(sumc[b + 1], card[b + 1], st, ct) == 0) ++b;
+  return (b + 1 >= M) || card[b + 1] == 0 || cmp_ratio(sumc[b + 1], card[b + 1], st, ct) < 0;
+}
+
+// Candidate a ranks before candidate b (b = -1: empty).
+__device__ __forceinline__ bool ranks_before(const uint64_t* card, const uint64_t* sumc, int a, int b) {
+  if (b < 0) return true;
+  const int c = cmp_ratio(sumc[a], card[a], sumc[b], card[b]);
+  return c > 0 || (c == 0 && a < b);
+}
+
+// A warp's sorted top list of L <= 32 candidates: lane r holds rank r (-1:
+// empty).  Inserts the candidates c of the 32 lanes (-1: none): each is first
+// tested against the list's last entry, and only those that beat it are
+// inserted one by one.  Called by all 32 lanes.
+__device__ __forceinline__ void topk_insert(const uint64_t* card, const uint64_t* sumc, int L, int& mine, int c) {
+  const int lane = threadIdx.x & 31;
+  const int last = __shfl_sync(0xffffffffu, mine, L - 1);
+  unsigned m = __ballot_sync(0xffffffffu, c >= 0 && ranks_before(card, sumc, c, last));
+  while (m) {
+    const int src = __ffs(m) - 1;
+    m &= m - 1;
+    const int tn = __shfl_sync(0xffffffffu, c, src);
+    const unsigned worse = __ballot_sync(0xffffffffu, lane < L && ranks_before(card, sumc, tn, mine));
+    if (!worse) continue;
+    const int pos = __ffs(worse) - 1;
+    const int up = __shfl_up_sync(0xffffffffu, mine, 1);
+    if (lane == pos) mine = tn;
+    else if (lane > pos && lane < L) mine = up;
+  }
+}
+
+// Block version (any M, any max_k).  `cand` is scratch for up to (M + 1) / 2 + 1
+// candidates; sh_int holds kShInts ints.
 __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, int M, int max_k, int32_t* out_t,
                                   int32_t* out_count, int32_t* out_t0, int32_t* cand, int* sh_int,
                                   uint64_t* scratch) {
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
   if (tid == 0) sh_int[0] = 0;
   __syncthreads();
-  // 1. plateau starts that are local maxima
-  for (int t = tid; t < M; t += nt) {
-    const uint64_t ct = card[t];
-    if (ct == 0) continue;
-    const uint64_t st = sumc[t];
-    bool start = true, left_lower = true;
-    if (t > 0 && card[t - 1] > 0) {
-      const int c = cmp_ratio(sumc[t - 1], card[t - 1], st, ct);
-      start = c != 0;
-      left_lower = c < 0;
-    }
-    if (!start || !left_lower) continue;
-    int b = t;
-    while (b + 1 < M && card[b + 1] > 0 && cmp_ratio(sumc[b + 1], card[b + 1], st, ct) == 0) ++b;
-    const bool right_lower = (b + 1 >= M) || card[b + 1] == 0 || cmp_ratio(sumc[b + 1], card[b + 1], st, ct) < 0;
-    if (right_lower) cand[atomicAdd(&sh_int[0], 1)] = t;
-  }
+  // 1. plateau starts that are local maxima (in no particular order)
+  for (int t = tid; t < M; t += nt)
+    if (is_max_start(card, sumc, M, t)) cand[atomicAdd(&sh_int[0], 1)] = t;
   __syncthreads();
   const int K = sh_int[0];
-  // 2. t0 (Eq. 4): best (C, -t) over valid t, block reduction via candidates is not
-  //    enough in general (t0 is always a local maximum, but compute it directly).
-  int best = -1;
-  for (int t = tid; t < M; t += nt) {
-    if (card[t] == 0) continue;
-    if (best < 0) { best = t; continue; }
-    const int c = cmp_ratio(sumc[t], card[t], sumc[best], card[best]);
-    if (c > 0) best = t;  // t increases within a thread, so ties keep the smaller t
-  }
-  // warp + block reduction of `best`
-  for (int o = 16; o > 0; o >>= 1) {
-    const int other = __shfl_down_sync(0xffffffffu, best, o);
-    if (other >= 0) {
-      if (best < 0) best = other;
-      else {
-        const int c = cmp_ratio(sumc[other], card[other], sumc[best], card[best]);
-        if (c > 0 || (c == 0 && other < best)) best = other;
+  if (K <= 64) {
+    // 2a. few maxima: the rank of a candidate is the number of candidates before
+    //     it, one warp per candidate, one comparison per lane and candidate
+    for (int i = warp; i < K; i += nw) {
+      const int ti = cand[i];
+      int before = 0;
+      for (int j = lane; j < K; j += 32) {
+        const int tj = cand[j];
+        if (tj != ti && ranks_before(card, sumc, tj, ti)) ++before;
+      }
+      before = __reduce_add_sync(0xffffffffu, before);
+      if (lane == 0) {
+        if (out_t && before < max_k) out_t[before] = ti;
+        if (before == 0 && out_t0) *out_t0 = ti;
       }
     }
+    if (out_t)
+      for (int r = K + tid; r < max_k; r += nt) out_t[r] = -1;
+    if (tid == 0) {
+      if (out_count) *out_count = K;
+      if (K == 0 && out_t0) *out_t0 = -1;
+    }
+    __syncthreads();
+    return;
   }
-  int* wbest = sh_int + 1;
-  if ((tid & 31) == 0) wbest[tid >> 5] = best;
+  // 2b. per-warp sorted top lists of the first L candidates in rank order, merged
+  //     by warp 0; with max_k > 32 the list only serves t0 (rank 0)
+  const int L = (max_k > 0 && max_k <= 32) ? max_k : 1;
+  int mine = -1;
+  for (int base = warp * 32; base < K; base += nt) topk_insert(card, sumc, L, mine, base + lane < K ? cand[base + lane] : -1);
+  int* lists = sh_int + 40;  // [nw][32] within the block's kShInts
+  lists[warp * 32 + lane] = mine;
   __syncthreads();
-  if (tid == 0) {
-    int b = -1;
-    for (int w = 0; w < nt / 32; ++w) {
-      const int o = wbest[w];
-      if (o < 0) continue;
-      if (b < 0) b = o;
-      else {
-        const int c = cmp_ratio(sumc[o], card[o], sumc[b], card[b]);
-        if (c > 0 || (c == 0 && o < b)) b = o;
-      }
+  if (warp == 0) {
+    for (int w = 1; w < nw; ++w) topk_insert(card, sumc, L, mine, lists[w * 32 + lane]);
+    if (out_t && max_k <= 32 && lane < max_k) out_t[lane] = mine;  // -1 where fewer than max_k maxima exist
+    if (lane == 0) {
+      if (out_t0) *out_t0 = mine;
+      if (out_count) *out_count = K;
     }
-    if (out_t0) *out_t0 = b;
-    if (out_count) *out_count = K;
   }
-  // 3. the first max_k candidates in rank order (C descending, then t ascending)
-  if (out_t && max_k > 0 && max_k <= 32) {
-    __syncthreads();  // sh_int[1..] held the warp winners of step 2
-    // each warp keeps a sorted list of its best candidates, lane r holding rank r
-    // (-1: empty); a batch of 32 candidates is first tested against the list's
-    // last entry, and only those that beat it are inserted one by one
-    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    auto better = [&](int a, int b) {  // candidate a ranks before b (b may be -1)
-      if (b < 0) return true;
-      const int c = cmp_ratio(sumc[a], card[a], sumc[b], card[b]);
-      return c > 0 || (c == 0 && a < b);
-    };
-    int mine = -1;
-    auto insert_batch = [&](int c) {  // c: this lane's candidate t or -1
-      const int last = __shfl_sync(0xffffffffu, mine, max_k - 1);
-      unsigned m = __ballot_sync(0xffffffffu, c >= 0 && better(c, last));
-      while (m) {
-        const int src = __ffs(m) - 1;
-        m &= m - 1;
-        const int tn = __shfl_sync(0xffffffffu, c, src);
-        const unsigned worse = __ballot_sync(0xffffffffu, lane < max_k && better(tn, mine));
-        if (!worse) continue;
-        const int pos = __ffs(worse) - 1;
-        const int up = __shfl_up_sync(0xffffffffu, mine, 1);
-        if (lane == pos) mine = tn;
-        else if (lane > pos && lane < max_k) mine = up;
-      }
-    };
-    for (int base = warp * 32; base < K; base += nt) insert_batch(base + lane < K ? cand[base + lane] : -1);
-    int* lists = sh_int + 40;  // [nw][32] within the block's kShInts
-    lists[warp * 32 + lane] = mine;
-    __syncthreads();
-    if (warp == 0) {
-      for (int w = 1; w < nw; ++w) insert_batch(lists[w * 32 + lane]);
-      if (lane < max_k) out_t[lane] = mine;  // -1 where fewer than max_k maxima exist
-    }
-    __syncthreads();
-  } else if (out_t) {
-    // any max_k: rank of each candidate = number of candidates before it
+  // 3. max_k > 32: rank of each candidate = number of candidates before it
+  if (out_t && max_k > 32) {
     for (int i = tid; i < K; i += nt) {
       const int ti = cand[i];
-      const uint64_t si = sumc[ti], ci = card[ti];
       int rank = 0;
       for (int j = 0; j < K && rank < max_k; ++j) {
         const int tj = cand[j];
-        if (tj == ti) continue;
-        const int c = cmp_ratio(sumc[tj], card[tj], si, ci);
-        if (c > 0 || (c == 0 && tj < ti)) ++rank;
+        if (tj != ti && ranks_before(card, sumc, tj, ti)) ++rank;
       }
       if (rank < max_k) out_t[rank] = ti;
     }
@@ -376,14 +386,16 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
     }
     __syncthreads();
     curve_epilogue<false>(hsm, hsm + bins, hsm + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
+    if (P.out_count)
+      select_thresholds(card_s, sumc_s, M, P.max_k, P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr,
+                        P.out_count + d.out, P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
   } else {
     curve_epilogue<true>(h, h + bins, h + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
     for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) h[b] = 0ull;
-  }
-  if (P.out_count) {
-    select_thresholds(stage_cs ? card_s : card, stage_cs ? sumc_s : sumc, M, P.max_k,
-                      P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr, P.out_count + d.out,
-                      P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
+    if (P.out_count)
+      select_thresholds(stage_cs ? card_s : card, stage_cs ? sumc_s : sumc, M, P.max_k,
+                        P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr, P.out_count + d.out,
+                        P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
   }
   if (threadIdx.x == 0) {
     if (P.out_status) P.out_status[d.out] = bad ? -3 : 0;  // KOHLER_ERR_RANGE / KOHLER_OK
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
   uint32_t* lo = hs + 2 * bins;
   uint32_t* cnt = lo + bins;
   int32_t* brd = reinterpret_cast<int32_t*>(cnt + bins);
-  __shared__ uint64_t scratch[40];
+  __shared__ uint64_t scratch[kScratch];
   __shared__ int sh_int[kShInts];
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -614,23 +626,16 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
   }
 }
 
-// ----------------------------------------------------------------------------- uint8 pass
-// The uint8 pass, written for few instructions per pixel.  A lane holds 8
-// pixels of a row, split into four registers of two 16-bit lanes:
+// ----------------------------------------------------------------------------- uint8 SWAR layout
+// A lane holds 8 pixels of a row, split into four registers of two 16-bit lanes:
 //   E0 = (p0, p2), O0 = (p1, p3), E1 = (p4, p6), O1 = (p5, p7),
 // each value multiplied by 4, so that register halves are ready-made byte
 // offsets of 32-bit shared-memory bins.  The right pairs of the row are then
 // (E0 -> O0), (O0 -> (p2, p4)), (E1 -> O1), (O1 -> (p6, p8)): two of the four
 // "right" registers are free and the other two take one byte permute each.
-// Flags use a bias of 1024 (values * 4 <= 1020).  Per-pixel bins are per warp
-// and packed (low 16 bits: 4 * n_lo, high 16 bits: pixel count); a warp
-// flushes them into the block's 32-bit totals every kPackRows rows.
+// Flags [second >= first] use a bias of 1024 per half (values * 4 <= 1020).
 namespace u8 {
 constexpr uint32_t B = 0x04000400u;   // bias per 16-bit lane
-constexpr uint32_t LOW = 0x00ff00ffu;
-constexpr uint32_t LOW4 = 0x03fc03fcu;
-constexpr int kPackRows = 15;         // 15 rows * 256 px * 16 < 65536
-constexpr int kWords = 512 + 3 * 256; // hs[512], lo[256], cnt[256], brd[256]; then pk[NW][256]
 
 // Shared-memory add at a 32-bit shared-window address (no return value).
 __device__ __forceinline__ void red_s(uint32_t addr, uint32_t v) {
@@ -641,547 +646,70 @@ struct Row {
   uint32_t E0, O0, E1, O1;  // 4 * (p0,p2), 4 * (p1,p3), 4 * (p4,p6), 4 * (p5,p7)
 };
 
-__device__ __forceinline__ Row unpack(uint2 r) {
-  Row v;
-  v.E0 = (r.x << 2) & LOW4;
-  v.O0 = (r.x >> 6) & LOW4;
-  v.E1 = (r.y << 2) & LOW4;
-  v.O1 = (r.y >> 6) & LOW4;
-  return v;
-}
-
 __device__ __forceinline__ uint32_t ge(uint32_t second, uint32_t first) { return (second + B - first) & B; }
 }  // namespace u8
 
-template <int NW, bool CHECK>
-__global__ void __launch_bounds__(NW * 32) k_u8(const __grid_constant__ LaunchParams P) {
-  using namespace u8;
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[kShInts];
-  unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
-  uint32_t* const hs = smem;        // byte offset 0
-  uint32_t* const lo = smem + 512;  // 2048
-  uint32_t* const cnt = smem + 768; // 3072
-  int32_t* const brd = reinterpret_cast<int32_t*>(smem + 1024);  // 4096
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // shared-window addresses fit 16 bits: add them to both lanes of a key register
-  const int words = kWords + NW * 256;
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-  const uint32_t pk_addr = sbase + (uint32_t)(kWords + warp * 256) * 4u;
-  const uint32_t PK2 = pk_addr | (pk_addr << 16);
-  const uint32_t HS2 = sbase | (sbase << 16);
-  if (sbase + (uint32_t)words * 4u >= 65536u) {  // shared addresses are block-relative and small
-    if (threadIdx.x == 0) atomicOr(P.sticky, kErrInternal);
-    return;
-  }
-  uint32_t* const mypk = smem + kWords + warp * 256;
-  for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
-  __syncthreads();
-  const uint32_t clamp4 = CHECK ? (uint32_t)(4 * (P.M - 1)) * 0x00010001u : 0u;
-
-  const int64_t T_all = P.total_rs;
-  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
-  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
-  int i = r0 < r1 ? image_of(P, r0) : 0;
-  while (r0 < r1) {
-    const ImgDesc& d = P.img[i];
-    const int BH = d.y1 - d.y0;
-    const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * BH);
-    const int64_t seg = seg_end - r0;
-    const int W = d.W, H = d.H;
-    const int64_t pitch = d.pitch;
-    uint32_t vmax = 0;
-    int pack_rows = 0;
-    int64_t a = r0 + (seg * warp) / NW;
-    const int64_t b = r0 + (seg * (warp + 1)) / NW;
-    while (a < b) {
-      const int64_t q = a - d.rs_begin;
-      const int strip = (int)(q / BH);
-      const int ya = d.y0 + (int)(q % BH);
-      const int yb = (int)min64((int64_t)d.y1, (int64_t)ya + (b - a));
-      a += yb - ya;
-      const int x0 = strip * 256 + lane * 8;
-      const bool act = x0 < W;
-      const bool lastlane = act && (x0 + 8 == W);
-      const bool need_right = act && !lastlane && lane == 31;
-      const bool need_left = act && x0 > 0 && lane == 0;
-      const bool edge_warp = (strip == 0) || ((strip + 1) * 256 >= W);  // holds x = 0 or x = W - 1
-      const unsigned char* rowp = d.base + (int64_t)ya * pitch + x0;
-      // prefetch ring: rows ya (current), ya + 1, ya + 2
-      auto ld = [&](const unsigned char* p, bool ok, uint2& raw, uint32_t& edge) {
-        raw = make_uint2(0u, 0u);
-        edge = 0u;
-        if (ok && act) {
-          raw = __ldg(reinterpret_cast<const uint2*>(p));
-          if (need_right) edge = __ldg(p + 8);
-          if (need_left) edge = __ldg(p - 1);
-        }
-      };
-      uint2 rc, pf0, pf1;
-      uint32_t ec, ef0, ef1;
-      ld(rowp, true, rc, ec);
-      ld(rowp + pitch, ya + 1 < H, pf0, ef0);
-      ld(rowp + 2 * pitch, ya + 2 < H && ya + 2 <= yb, pf1, ef1);
-      Row V = unpack(rc);
-      if (CHECK) {
-        vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V.E0, V.O0)), __vmaxu2(V.E1, V.O1));
-        V.E0 = __vminu2(V.E0, clamp4); V.O0 = __vminu2(V.O0, clamp4);
-        V.E1 = __vminu2(V.E1, clamp4); V.O1 = __vminu2(V.O1, clamp4);
-      }
-      uint32_t UE0 = B, UO0 = B, UE1 = B, UO1 = B;  // flags of pairs (upper -> p); B: no upper pair
-      if (ya > 0) {
-        uint2 ru;
-        uint32_t eu;
-        ld(rowp - pitch, true, ru, eu);
-        Row U = unpack(ru);
-        if (CHECK) {
-          U.E0 = __vminu2(U.E0, clamp4); U.O0 = __vminu2(U.O0, clamp4);
-          U.E1 = __vminu2(U.E1, clamp4); U.O1 = __vminu2(U.O1, clamp4);
-        }
-        UE0 = ge(V.E0, U.E0); UO0 = ge(V.O0, U.O0); UE1 = ge(V.E1, U.E1); UO1 = ge(V.O1, U.O1);
-      }
-      for (int y = ya; y < yb; ++y) {
-        const bool has_down = y + 1 < H;
-        const uint2 rn = pf0;
-        const uint32_t en = ef0;
-        pf0 = pf1;
-        ef0 = ef1;
-        ld(rowp + 3 * pitch, y + 3 < H && y + 3 <= yb, pf1, ef1);
-        Row N = unpack(rn);
-        if (CHECK) {
-          vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(N.E0, N.O0)), __vmaxu2(N.E1, N.O1));
-          N.E0 = __vminu2(N.E0, clamp4); N.O0 = __vminu2(N.O0, clamp4);
-          N.E1 = __vminu2(N.E1, clamp4); N.O1 = __vminu2(N.O1, clamp4);
-        }
-        // right neighbour of p7: p0 of the next lane, the next strip's first pixel,
-        // or (last column) p7 itself, which pads the missing pair with an equal one
-        uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
-        if (need_right) nb = CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2;
-        if (lastlane) nb = V.O1 >> 16;
-        const uint32_t E0s = prmt<0x5432u>(V.E0, V.E1);  // (p2, p4)
-        const uint32_t E1s = prmt<0x5432u>(V.E1, nb);    // (p6, p8)
-        // flags [second >= first] of the right pairs, per register of first pixels
-        const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
-        // lower pairs
-        uint32_t DE0 = 0, DO0 = 0, DE1 = 0, DO1 = 0;
-        if (has_down) { DE0 = ge(N.E0, V.E0); DO0 = ge(N.O0, V.O0); DE1 = ge(N.E1, V.E1); DO1 = ge(N.O1, V.O1); }
-        // pair (p-1 -> p0): from the previous lane's last right pair, or the left
-        // strip's last pixel (value 0 at x = 0: flag 1, i.e. no contribution)
-        uint32_t gl = __shfl_up_sync(0xffffffffu, GO1, 1);
-        if (lane == 0) {
-          const uint32_t el4 = need_left ? (CHECK ? min(ec, (uint32_t)(P.M - 1)) << 2 : ec << 2) : 0u;
-          gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
-        }
-        const uint32_t LE0 = prmt<0x5432u>(gl, GO0);   // pairs ending at p0, p2
-        const uint32_t LE1 = prmt<0x5432u>(GO0, GO1);  // pairs ending at p4, p6
-        // n_lo * 1024 per pixel: [right >= p] + [lower >= p] + [left > p] + [upper > p]
-        const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
-        const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
-        const uint32_t nE1 = (GE1 + DE1 + 2 * B) - (LE1 + UE1);
-        const uint32_t nO1 = (GO1 + DO1 + 2 * B) - (GE1 + UO1);
-        if (act) {
-          // per-pixel packed bins: payload (4 n_lo) | (1 << 16)
-          const uint32_t aE0 = V.E0 + PK2, aO0 = V.O0 + PK2, aE1 = V.E1 + PK2, aO1 = V.O1 + PK2;
-          red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, 0x00010000u));
-          red_s(aE0 >> 16, prmt<0x7603u>(nE0, 0x00010000u));
-          red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, 0x00010000u));
-          red_s(aO0 >> 16, prmt<0x7603u>(nO0, 0x00010000u));
-          red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, 0x00010000u));
-          red_s(aE1 >> 16, prmt<0x7603u>(nE1, 0x00010000u));
-          red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, 0x00010000u));
-          red_s(aO1 >> 16, prmt<0x7603u>(nO1, 0x00010000u));
-          // pair sums s = f(p) + f(q): shared addresses of hs[s]
-          const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
-          const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
-          red_s(sE0 & 0xffffu, 1u);
-          red_s(sE0 >> 16, 1u);
-          red_s(sO0 & 0xffffu, 1u);
-          red_s(sO0 >> 16, 1u);
-          red_s(sE1 & 0xffffu, 1u);
-          red_s(sE1 >> 16, 1u);
-          red_s(sO1 & 0xffffu, 1u);
-          red_s(sO1 >> 16, 1u);
-          if (has_down) {
-            const uint32_t dE0 = V.E0 + N.E0 + HS2, dO0 = V.O0 + N.O0 + HS2;
-            const uint32_t dE1 = V.E1 + N.E1 + HS2, dO1 = V.O1 + N.O1 + HS2;
-            red_s(dE0 & 0xffffu, 1u);
-            red_s(dE0 >> 16, 1u);
-            red_s(dO0 & 0xffffu, 1u);
-            red_s(dO0 >> 16, 1u);
-            red_s(dE1 & 0xffffu, 1u);
-            red_s(dE1 >> 16, 1u);
-            red_s(dO1 & 0xffffu, 1u);
-            red_s(dO1 >> 16, 1u);
-          }
-          // border deficits 4 - deg(p); the padded right pair of the last column
-          // counts -1 (its partner is absent)
-          if (y == 0 || !has_down) {
-            const int rowb = (y == 0 ? 1 : 0) + (has_down ? 0 : 1);
-            const uint32_t vv[4] = {V.E0, V.O0, V.E1, V.O1};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              atomicAdd(&brd[(vv[k] & 0xffffu) >> 2], rowb);
-              atomicAdd(&brd[vv[k] >> 18], rowb);
-            }
-          }
-          if (edge_warp) {
-            if (x0 == 0) atomicAdd(&brd[(V.E0 & 0xffffu) >> 2], 1);
-            if (lastlane) atomicAdd(&brd[V.O1 >> 18], -1);
-          }
-        }
-        V = N;
-        UE0 = DE0; UO0 = DO0; UE1 = DE1; UO1 = DO1;
-        ec = en;
-        rowp += pitch;
-        if (++pack_rows == kPackRows) {
-          __syncwarp();
-          asm volatile("" ::: "memory");
-          for (int v = lane; v < 256; v += 32) {
-            const uint32_t w = mypk[v];
-            if (w) {
-              atomicAdd(&lo[v], (w & 0xffffu) >> 2);
-              atomicAdd(&cnt[v], w >> 16);
-              mypk[v] = 0u;
-            }
-          }
-          __syncwarp();
-          pack_rows = 0;
-        }
-      }
-    }
-    if (CHECK && ((vmax & 0xffffu) > 4u * (uint32_t)(P.M - 1) || (vmax >> 16) > 4u * (uint32_t)(P.M - 1)))
-      atomicOr(P.err + d.slot, kErrRange);
-    __syncwarp();
-    asm volatile("" ::: "memory");
-    for (int v = lane; v < 256; v += 32) {
-      const uint32_t w = mypk[v];
-      if (w) {
-        atomicAdd(&lo[v], (w & 0xffffu) >> 2);
-        atomicAdd(&cnt[v], w >> 16);
-        mypk[v] = 0u;
-      }
-    }
-    __syncthreads();
-    flush_cta(P, i, hs, lo, cnt, brd, 256);
-    __syncthreads();
-    image_rows_done(P, i, seg, scratch, sh_int, sb, (size_t)P.smem_bytes);
-    for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
-    __syncthreads();
-    r0 = seg_end;
-    ++i;
-  }
-}
-
-// ----------------------------------------------------------------------------- uint8 tile pass
-// Same arithmetic as k_u8, with two changes for the shared-memory atomic unit.
-// (1) A warp is laid over a tile of 32 columns x 8 rows: lane l holds the 8
-// pixels x = xs + 8 (l & 3) .. + 7 of row y = ty + (l >> 2), so the 32 keys of
-// one update come from a compact 32 x 8 patch and fall into few distinct values.
-// Vertical neighbours come from the lane 4 positions away (a lower row of the
-// tile, or, for the tile's last row, the next tile's first row that lane (c, 0)
-// has already prefetched); the flags of the upper pairs come from the lane above
-// (for the first row: from lane (c, 7) of the previous tile).  A warp walks down
-// a 32-column strip.
-// (2) Updates that add the same value in every lane merge lanes that hit the
-// same word, so the pair-sum bins (which add 1) need one copy; the packed
-// per-pixel bins add different values, and there each of the 32 lanes adds into
-// its own copy (word v * 32 + lane: the bank is the lane), shared by the warps of
-// the block.  The copies are folded at the end of each image segment; the grid
-// is sized so that a warp reduces at most kMaxTilesPerWarp tiles of a segment,
-// which keeps the 16-bit fields of a copy below 2^16.
-// Work unit: one tile (32 x 8).  Requirements as for k_u8.
-namespace u8t {
-constexpr int kCopies = 32;
-constexpr int kPkWords = 256 * kCopies;        // per-lane copies of the packed pixel bins
-constexpr int kWords = kPkWords + 512 + 3 * 256; // + hs[512], lo[256], cnt[256], brd[256]
-constexpr int kMaxTilesPerWarp = 60;           // 8 warps * 60 tiles * 8 px * 16 < 2^16
-}  // namespace u8t
-
-template <int NW, bool CHECK>
-__global__ void __launch_bounds__(NW * 32, (NW == 8 ? 4 : 1)) k_u8t(const __grid_constant__ LaunchParams P) {
-  using namespace u8;
-  extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint64_t scratch[40];
-  __shared__ int sh_int[kShInts];
-  unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
-  uint32_t* const pk = smem;                                  // [256][32]
-  uint32_t* const hs = smem + u8t::kPkWords;                  // [512]
-  uint32_t* const lo = hs + 512;
-  uint32_t* const cnt = lo + 256;
-  int32_t* const brd = reinterpret_cast<int32_t*>(cnt + 256);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int c = lane & 3, r = lane >> 2;
-  const int words = u8t::kWords;
-  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-  // 16-bit shared addresses in each lane of a key register: pixel bin of value v
-  // at sbase + 128 v + 4 lane, pair-sum bin of s at hs + 4 s
-  const uint32_t pk_addr = sbase + 4u * (uint32_t)lane;
-  const uint32_t PK2 = pk_addr | (pk_addr << 16);
-  const uint32_t hs_addr = sbase + 4u * (uint32_t)u8t::kPkWords;
-  const uint32_t HS2 = hs_addr | (hs_addr << 16);
-  if (hs_addr + 4u * 512u >= 65536u) {  // shared addresses are block-relative and small
-    if (threadIdx.x == 0) atomicOr(P.sticky, kErrInternal);
-    return;
-  }
-  for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
-  __syncthreads();
-  allow_dependents();
-  const uint32_t clamp4 = CHECK ? (uint32_t)(4 * (P.M - 1)) * 0x00010001u : 0u;
-  const uint32_t lastv4 = (uint32_t)(4 * (P.M - 1));
-  const int src_dn = (lane + 4) & 31, src_up = (lane + 28) & 31;
-
-  const int64_t T_all = P.total_rs;
-  int64_t r0 = (T_all * blockIdx.x) / gridDim.x;
-  const int64_t r1 = (T_all * (blockIdx.x + 1)) / gridDim.x;
-  int i = r0 < r1 ? image_of(P, r0) : 0;
-  while (r0 < r1) {
-    const ImgDesc& d = P.img[i];
-    const int tiles = (d.y1 - d.y0 + 7) >> 3;
-    const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * tiles);
-    const int64_t seg = seg_end - r0;
-    const int W = d.W, H = d.H;
-    const int64_t pitch = d.pitch;
-    uint32_t vmax = 0;
-    int64_t a = r0 + (seg * warp) / NW;
-    const int64_t b = r0 + (seg * (warp + 1)) / NW;
-    while (a < b) {
-      const uint32_t q = (uint32_t)(a - d.rs_begin);  // < 2^32 units per image (checked on the host)
-      const int strip = (int)(q / (uint32_t)tiles);
-      const int ta = (int)(q - (uint32_t)strip * (uint32_t)tiles);
-      const int tb = (int)min64((int64_t)tiles, (int64_t)ta + (b - a));
-      a += tb - ta;
-      const int x0 = strip * 32 + c * 8;
-      const bool act = x0 < W;
-      const bool lastcol = act && (x0 + 8 == W);
-      const bool need_right = act && !lastcol && c == 3;
-      const bool need_left = act && x0 > 0 && c == 0;
-      const bool edge_strip = (strip == 0) || ((strip + 1) * 32 >= W);
-      const int ys = d.y0 + 8 * ta;          // first row of the run (tile row 0)
-      // Loads never branch: a row past the image reads the last row, a lane past
-      // the image width reads the row's last 8 pixels, a lane without a strip-edge
-      // pixel reads its own first pixel; none of these is ever reduced.
-      const unsigned char* colp = d.base + (act ? x0 : W - 8);
-      const int eoff = need_right ? 8 : (need_left ? -1 : 0);
-      int y = ys + r;                        // this lane's row in the current tile
-      auto ld = [&](int yy, uint2& raw, uint32_t& edge4) {
-        const unsigned char* p = colp + (int64_t)min(yy, H - 1) * pitch;
-        raw = __ldg(reinterpret_cast<const uint2*>(p));
-        const uint32_t e = __ldg(p + eoff);
-        edge4 = CHECK ? min(e << 2, lastv4) : e << 2;
-      };
-      auto clampv = [&](Row& v) {
-        if (CHECK) {
-          v.E0 = __vminu2(v.E0, clamp4); v.O0 = __vminu2(v.O0, clamp4);
-          v.E1 = __vminu2(v.E1, clamp4); v.O1 = __vminu2(v.O1, clamp4);
-        }
-      };
-      uint2 rc, pf0, pf1;
-      uint32_t ec, ef0, ef1;
-      ld(y, rc, ec);
-      ld(y + 8, pf0, ef0);
-      ld(y + 16, pf1, ef1);
-      Row V = unpack(rc);
-      if (CHECK) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V.E0, V.O0)), __vmaxu2(V.E1, V.O1));
-      clampv(V);
-      // flags of the pairs (row ys - 1 -> row ys) for lane (c, 0), handed to
-      // lane (c, 7) as if it had computed them for a previous tile
-      uint32_t DpE0, DpO0, DpE1, DpO1;
-      {
-        uint2 ru;
-        uint32_t eu;
-        ld(ys - 1 + (ys == 0), ru, eu);
-        Row U = unpack(ru);
-        clampv(U);
-        uint32_t fE0 = B, fO0 = B, fE1 = B, fO1 = B;
-        if (ys > 0) { fE0 = ge(V.E0, U.E0); fO0 = ge(V.O0, U.O0); fE1 = ge(V.E1, U.E1); fO1 = ge(V.O1, U.O1); }
-        DpE0 = __shfl_sync(0xffffffffu, fE0, src_dn);  // lane (c, 7) takes lane (c, 0)'s flags
-        DpO0 = __shfl_sync(0xffffffffu, fO0, src_dn);
-        DpE1 = __shfl_sync(0xffffffffu, fE1, src_dn);
-        DpO1 = __shfl_sync(0xffffffffu, fO1, src_dn);
-      }
-      for (int t = ta; t < tb; ++t) {
-        const uint2 rn = pf0;
-        const uint32_t en = ef0;
-        pf0 = pf1;
-        ef0 = ef1;
-        ld(y + 24, pf1, ef1);
-        // this lane's row of the next tile, and the lower row: from lane (c, r + 1),
-        // or for r = 7 from lane (c, 0)'s row of the next tile
-        Row Vn = unpack(rn);
-        if (CHECK) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(Vn.E0, Vn.O0)), __vmaxu2(Vn.E1, Vn.O1));
-        clampv(Vn);
-        Row N;
-        N.E0 = __shfl_sync(0xffffffffu, r == 0 ? Vn.E0 : V.E0, src_dn);
-        N.O0 = __shfl_sync(0xffffffffu, r == 0 ? Vn.O0 : V.O0, src_dn);
-        N.E1 = __shfl_sync(0xffffffffu, r == 0 ? Vn.E1 : V.E1, src_dn);
-        N.O1 = __shfl_sync(0xffffffffu, r == 0 ? Vn.O1 : V.O1, src_dn);
-        const bool proc = act && y < d.y1;   // rows of this band only
-        const bool has_down = y + 1 < H;
-        // right neighbour of p7
-        uint32_t nb = __shfl_down_sync(0xffffffffu, V.E0, 1);
-        if (need_right) nb = ec;
-        if (lastcol) nb = V.O1 >> 16;
-        const uint32_t E0s = prmt<0x5432u>(V.E0, V.E1);  // (p2, p4)
-        const uint32_t E1s = prmt<0x5432u>(V.E1, nb);    // (p6, p8)
-        const uint32_t GE0 = ge(V.O0, V.E0), GO0 = ge(E0s, V.O0), GE1 = ge(V.O1, V.E1), GO1 = ge(E1s, V.O1);
-        uint32_t DE0 = 0, DO0 = 0, DE1 = 0, DO1 = 0;
-        if (has_down) { DE0 = ge(N.E0, V.E0); DO0 = ge(N.O0, V.O0); DE1 = ge(N.E1, V.E1); DO1 = ge(N.O1, V.O1); }
-        // upper pairs: flags computed by the lane above (lane (c, 7) offers its previous tile's)
-        const uint32_t UE0 = __shfl_sync(0xffffffffu, r == 7 ? DpE0 : DE0, src_up);
-        const uint32_t UO0 = __shfl_sync(0xffffffffu, r == 7 ? DpO0 : DO0, src_up);
-        const uint32_t UE1 = __shfl_sync(0xffffffffu, r == 7 ? DpE1 : DE1, src_up);
-        const uint32_t UO1 = __shfl_sync(0xffffffffu, r == 7 ? DpO1 : DO1, src_up);
-        DpE0 = DE0; DpO0 = DO0; DpE1 = DE1; DpO1 = DO1;
-        // pair (p-1 -> p0)
-        uint32_t gl = __shfl_up_sync(0xffffffffu, GO1, 1);
-        if (c == 0) {
-          const uint32_t el4 = need_left ? ec : 0u;
-          gl = (((V.E0 & 0xffffu) + 1024u - el4) & 1024u) << 16;
-        }
-        const uint32_t LE0 = prmt<0x5432u>(gl, GO0);
-        const uint32_t LE1 = prmt<0x5432u>(GO0, GO1);
-        const uint32_t nE0 = (GE0 + DE0 + 2 * B) - (LE0 + UE0);
-        const uint32_t nO0 = (GO0 + DO0 + 2 * B) - (GE0 + UO0);
-        const uint32_t nE1 = (GE1 + DE1 + 2 * B) - (LE1 + UE1);
-        const uint32_t nO1 = (GO1 + DO1 + 2 * B) - (GE1 + UO1);
-        if (proc) {
-          const uint32_t aE0 = (V.E0 << 5) + PK2, aO0 = (V.O0 << 5) + PK2;
-          const uint32_t aE1 = (V.E1 << 5) + PK2, aO1 = (V.O1 << 5) + PK2;
-          red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, 0x00010000u));
-          red_s(aE0 >> 16, prmt<0x7603u>(nE0, 0x00010000u));
-          red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, 0x00010000u));
-          red_s(aO0 >> 16, prmt<0x7603u>(nO0, 0x00010000u));
-          red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, 0x00010000u));
-          red_s(aE1 >> 16, prmt<0x7603u>(nE1, 0x00010000u));
-          red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, 0x00010000u));
-          red_s(aO1 >> 16, prmt<0x7603u>(nO1, 0x00010000u));
-          const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
-          const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
-          red_s(sE0 & 0xffffu, 1u);
-          red_s(sE0 >> 16, 1u);
-          red_s(sO0 & 0xffffu, 1u);
-          red_s(sO0 >> 16, 1u);
-          red_s(sE1 & 0xffffu, 1u);
-          red_s(sE1 >> 16, 1u);
-          red_s(sO1 & 0xffffu, 1u);
-          red_s(sO1 >> 16, 1u);
-          if (has_down) {
-            const uint32_t dE0 = V.E0 + N.E0 + HS2, dO0 = V.O0 + N.O0 + HS2;
-            const uint32_t dE1 = V.E1 + N.E1 + HS2, dO1 = V.O1 + N.O1 + HS2;
-            red_s(dE0 & 0xffffu, 1u);
-            red_s(dE0 >> 16, 1u);
-            red_s(dO0 & 0xffffu, 1u);
-            red_s(dO0 >> 16, 1u);
-            red_s(dE1 & 0xffffu, 1u);
-            red_s(dE1 >> 16, 1u);
-            red_s(dO1 & 0xffffu, 1u);
-            red_s(dO1 >> 16, 1u);
-          }
-          if (y == 0 || !has_down) {
-            const int rowb = (y == 0 ? 1 : 0) + (has_down ? 0 : 1);
-            const uint32_t vv[4] = {V.E0, V.O0, V.E1, V.O1};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              atomicAdd(&brd[(vv[k] & 0xffffu) >> 2], rowb);
-              atomicAdd(&brd[vv[k] >> 18], rowb);
-            }
-          }
-          if (edge_strip) {
-            if (x0 == 0) atomicAdd(&brd[(V.E0 & 0xffffu) >> 2], 1);
-            if (lastcol) atomicAdd(&brd[V.O1 >> 18], -1);
-          }
-        }
-        V = Vn;
-        ec = en;
-        y += 8;
-      }
-    }
-    wait_prior();
-    if (CHECK && ((vmax & 0xffffu) > lastv4 || (vmax >> 16) > lastv4)) atomicOr(P.err + d.slot, kErrRange);
-    __syncthreads();
-    // fold the 32 copies of each pixel bin: warp w takes bins w, w + NW, ...
-    for (int v = warp; v < 256; v += NW) {
-      const uint32_t w = pk[v * 32 + lane];
-      pk[v * 32 + lane] = 0u;
-      const uint32_t l4 = __reduce_add_sync(0xffffffffu, w & 0xffffu);
-      const uint32_t n = __reduce_add_sync(0xffffffffu, w >> 16);
-      if (lane == 0) {
-        lo[v] += l4 >> 2;
-        cnt[v] += n;
-      }
-    }
-    __syncthreads();
-    flush_cta(P, i, hs, lo, cnt, brd, 256);
-    __syncthreads();
-    image_rows_done(P, i, seg, scratch, sh_int, sb, (size_t)P.smem_bytes);
-    r0 = seg_end;
-    ++i;
-    if (r0 < r1) {  // another image follows: the epilogue may have used the bins as scratch
-      for (int k = threadIdx.x; k < words; k += blockDim.x) smem[k] = 0u;
-      __syncthreads();
-    }
-  }
-}
-
 // ----------------------------------------------------------------------------- uint8 row-walk pass
-// Same arithmetic as k_u8t, laid out for fewer instructions per pixel.  Lane l
-// of a warp holds the 8 pixels x = xs + 8 l .. + 7 of one row of a 256-column
-// strip, and the warp walks down the strip: the lower row is the lane's own next
-// load and the flags of the upper pairs are its own previous row's, so a row
-// needs two shuffles (the right neighbour of p7 and the flag of the pair left of
-// p0).  Rows stream into a per-warp ring in shared memory with cp.async,
-// kRing - 1 rows ahead of the row being reduced, so load latency stays hidden
-// without registers.  Work unit: one row of one strip, numbered strip by strip,
-// so a warp's consecutive units continue its walk.  Blocks of 16 warps work in rounds: in a
-// round each warp reduces at most kUnitsPerRound units (32 rows), then the block
-// folds its per-lane bins and flushes every bin to the image's global
-// histograms, which bounds the packed 16-bit fields (a copy gains at most
-// 4 * 25 per 8 pixels of a row: 7 pairs inside the run, 16 vertical, 2 at its
-// ends) and keeps every shared counter far from overflow.
+// The uint8 pass (M <= 256), in the SWAR layout above.
+//
+// Strips and lanes.  A warp walks down a strip of 240 columns: lane l holds the
+// 8 pixels x = 240 s + 8 (l - 1) .. + 7 of the current row, so lanes 1..30 own
+// the strip's pixels and lanes 0 and 31 hold the last 8 pixels of the strip on
+// the left and the first 8 of the strip on the right.  Those two context lanes
+// make no update; they only feed the two shuffles of a row step (the right
+// neighbour of p7 and the flag of the pair left of p0), so strip edges need no
+// special case.  Left of the image a context lane holds zeros, which makes the
+// left-pair flag 1 (no contribution); right of the image the last column pads
+// its missing pair with an equal one, as in the other passes.
+//
+// Rows.  The lower row is the lane's own next row and the flags of the upper
+// pairs are its own previous row's.  Rows stream into a per-warp ring in shared
+// memory with cp.async, 2 kRingPairs - 1 rows ahead of the one being reduced,
+// two rows per slot, and each step reduces two rows.
+//
+// Bins.  The packed per-pixel payload is 4 n_lo(p) | deg(p) << 16, where deg is
+// the number of pair ends at p: 4, less one per missing upper, lower or left
+// neighbour; in the last column the missing right pair is replaced by the equal
+// padding pair (p7, p7), both of whose ends are at p7, so there deg is one more.
+// Summed per value, the high field gives H_lo + H_hi, so H_hi needs no border
+// histogram.  The payload differs between lanes, so each lane adds into its own
+// copy (word v * 32 + lane: the bank is the lane); the pair sums add 1 and keep
+// one copy.
+//
+// Work unit: one row of one strip, numbered strip by strip, so a warp's
+// consecutive units continue its walk.  Blocks of 16 warps work in rounds: in a
+// round each warp reduces at most kUnitsPerRound rows, then the block folds its
+// copies and flushes every bin to the image's global histograms.  That bounds
+// the packed 16-bit fields: per 8 pixels of a row a copy gains at most 4 * 25 in
+// the n_lo field (7 pairs inside the run, 16 vertical, 2 at its ends) and 33 in
+// the degree field.
 // Requirements (checked on the host): W % 8 == 0, base and pitch multiples of 8.
 namespace u8r {
 constexpr int kNW = 16;                        // warps per block
 constexpr int kUnitRows = 1;                   // rows per work unit
 constexpr int kUnitsPerRound = 32;             // units per warp between folds
-constexpr int kStripPx = 256;                  // columns per strip (32 lanes x 8 pixels)
+constexpr int kStripPx = 240;                  // owned columns per strip (lanes 1..30)
 constexpr int kRingPairs = 4;                  // row pairs in flight per warp (cp.async ring)
 constexpr int kPkWords = 256 * 32;             // per-lane copies of the packed pixel bins
-constexpr int kBinWords = kPkWords + 512 + 256;            // + hs[512], brd[256]
-constexpr int kRingWords = kNW * kRingPairs * (128 + 4);   // per warp and pair: 32 lanes x 16 bytes + 4 edge words
+constexpr int kBinWords = kPkWords + 512;      // + hs[512]
+constexpr int kRingWords = kNW * kRingPairs * 128;  // per warp and slot: 32 lanes x 16 bytes (two rows)
 constexpr int kWords = kBinWords + kRingWords;
 static_assert(kNW * kUnitRows * kUnitsPerRound * 100 < 65536, "packed n_lo field overflow");
-static_assert(kNW * kUnitRows * kUnitsPerRound * 8 < 65536, "packed count field overflow");
+static_assert(kNW * kUnitRows * kUnitsPerRound * 33 < 65536, "packed degree field overflow");
 }  // namespace u8r
 
-// Asynchronous global -> shared copies (cp.async, per thread; a thread's own
-// copies are visible to it after cp_wait).
-__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g, bool pred) {
-  asm volatile("{ .reg .pred p; setp.ne.b32 p, %2, 0; @p cp.async.ca.shared.global [%0], [%1], 8; }" ::"r"(saddr),
-               "l"(g), "r"((int)pred)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async4(uint32_t saddr, const void* g, bool pred) {
-  asm volatile("{ .reg .pred p; setp.ne.b32 p, %2, 0; @p cp.async.ca.shared.global [%0], [%1], 4; }" ::"r"(saddr),
-               "l"(g), "r"((int)pred)
-               : "memory");
+// Asynchronous global -> shared copy of 8 bytes; `bytes` (8 or 0) of them are
+// read, the rest of the destination is zero-filled (cp.async src-size).  A
+// thread's own copies are visible to it after cp_wait.
+__device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g, uint32_t bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(saddr), "l"(g), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ uint2 lds64(uint32_t saddr) {
-  uint2 v;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(saddr) : "memory");
-  return v;
-}
 __device__ __forceinline__ uint4 lds128(uint32_t saddr) {
   uint4 v;
   asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(saddr) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint32_t lds32(uint32_t saddr) {
-  uint32_t v;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(saddr) : "memory");
   return v;
 }
 // Pixels (b0, b1, b2, b3) of a word as 16-bit lanes scaled by 4: (b0, b2) and (b1, b3).
@@ -1195,23 +723,24 @@ __device__ __forceinline__ u8::Row unpack_p(uint2 r) {
 }
 
 // The 24 shared-memory updates of one row of 8 pixels (V, with lower row N):
-// per pixel its packed bin (value, payload 4 n_lo | 1 << 16), the pair sum of
-// its right pair (E0s, E1s carry p2, p4 / p6, p8) and, if the row has a lower
-// row, of its lower pair.
+// per pixel its packed bin (payload 4 n_lo | deg << 16; DEG holds deg << 16,
+// DEG0 and DEG7 the same for p0 and p7), the pair sum of its right pair (E0s, E1s
+// carry p2, p4 / p6, p8) and, if the row has a lower row, of its lower pair.
 __device__ __forceinline__ void u8r_row_updates(const u8::Row& V, const u8::Row& N, uint32_t E0s, uint32_t E1s,
-                                                uint32_t nE0, uint32_t nO0, uint32_t nE1, uint32_t nO1, uint32_t PK2,
-                                                uint32_t HS2, bool has_down) {
+                                                uint32_t nE0, uint32_t nO0, uint32_t nE1, uint32_t nO1, uint32_t DEG,
+                                                uint32_t DEG0, uint32_t DEG7, uint32_t PK2, uint32_t HS2,
+                                                bool has_down) {
   using u8::red_s;
   const uint32_t aE0 = (V.E0 << 5) + PK2, aO0 = (V.O0 << 5) + PK2;
   const uint32_t aE1 = (V.E1 << 5) + PK2, aO1 = (V.O1 << 5) + PK2;
-  red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, 0x00010000u));
-  red_s(aE0 >> 16, prmt<0x7603u>(nE0, 0x00010000u));
-  red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, 0x00010000u));
-  red_s(aO0 >> 16, prmt<0x7603u>(nO0, 0x00010000u));
-  red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, 0x00010000u));
-  red_s(aE1 >> 16, prmt<0x7603u>(nE1, 0x00010000u));
-  red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, 0x00010000u));
-  red_s(aO1 >> 16, prmt<0x7603u>(nO1, 0x00010000u));
+  red_s(aE0 & 0xffffu, prmt<0x7601u>(nE0, DEG0));
+  red_s(aE0 >> 16, prmt<0x7603u>(nE0, DEG));
+  red_s(aO0 & 0xffffu, prmt<0x7601u>(nO0, DEG));
+  red_s(aO0 >> 16, prmt<0x7603u>(nO0, DEG));
+  red_s(aE1 & 0xffffu, prmt<0x7601u>(nE1, DEG));
+  red_s(aE1 >> 16, prmt<0x7603u>(nE1, DEG));
+  red_s(aO1 & 0xffffu, prmt<0x7601u>(nO1, DEG));
+  red_s(aO1 >> 16, prmt<0x7603u>(nO1, DEG7));
   const uint32_t sE0 = V.E0 + V.O0 + HS2, sO0 = V.O0 + E0s + HS2;
   const uint32_t sE1 = V.E1 + V.O1 + HS2, sO1 = V.O1 + E1s + HS2;
   red_s(sE0 & 0xffffu, 1u);
@@ -1236,44 +765,31 @@ __device__ __forceinline__ void u8r_row_updates(const u8::Row& V, const u8::Row&
   }
 }
 
-// Border deficit `rowb` (missing upper and/or lower neighbours) for the 8 pixels of V.
-__device__ __forceinline__ void u8r_row_border(int32_t* brd, const u8::Row& V, int rowb) {
-  const uint32_t vv[4] = {V.E0, V.O0, V.E1, V.O1};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    atomicAdd(&brd[(vv[k] & 0xffffu) >> 2], rowb);
-    atomicAdd(&brd[vv[k] >> 18], rowb);
-  }
-}
-
 // Folds the 32 per-lane copies of every packed bin and flushes all bins of the
 // block into image i's global histograms, leaving them zero.  512 threads:
 // thread t sums half (t & 1) of bin t >> 1, reading its four 16-byte chunks in
 // an order rotated by the bin so that the 8 threads of a quarter warp hit
 // distinct banks.
-__device__ __forceinline__ void u8r_fold_flush(const LaunchParams& P, int i, uint32_t* pk, uint32_t* hs, int32_t* brd) {
+__device__ __forceinline__ void u8r_fold_flush(const LaunchParams& P, int i, uint32_t* pk, uint32_t* hs) {
   unsigned long long* g = P.hist + (size_t)P.img[i].slot * 4 * 256;
   const int t = threadIdx.x;
   const int v = t >> 1, h = t & 1;
   uint4* const row = reinterpret_cast<uint4*>(pk + v * 32 + h * 16);
-  uint32_t l4 = 0, n = 0;
+  uint32_t l4 = 0, dg = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int c = (k + v) & 3;
     const uint4 w = row[c];
     row[c] = make_uint4(0u, 0u, 0u, 0u);
     l4 += (w.x & 0xffffu) + (w.y & 0xffffu) + (w.z & 0xffffu) + (w.w & 0xffffu);
-    n += (w.x >> 16) + (w.y >> 16) + (w.z >> 16) + (w.w >> 16);
+    dg += (w.x >> 16) + (w.y >> 16) + (w.z >> 16) + (w.w >> 16);
   }
   l4 += __shfl_xor_sync(0xffffffffu, l4, 1);
-  n += __shfl_xor_sync(0xffffffffu, n, 1);
+  dg += __shfl_xor_sync(0xffffffffu, dg, 1);
   if (h == 0) {
     const uint32_t l = l4 >> 2;
-    const int32_t r = brd[v];
-    brd[v] = 0;
-    const long long hi = 4ll * (long long)n - (long long)r - (long long)l;
-    if (l) atomicAdd(g + v, (unsigned long long)l);
-    if (hi) atomicAdd(g + 256 + v, (unsigned long long)hi);
+    if (l) atomicAdd(g + v, (unsigned long long)l);               // H_lo
+    if (dg - l) atomicAdd(g + 256 + v, (unsigned long long)(dg - l));  // H_hi = (H_lo + H_hi) - H_lo
   }
   const uint32_t s = hs[t];
   hs[t] = 0u;
@@ -1285,13 +801,12 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
   using namespace u8;
   constexpr int NW = u8r::kNW;
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint64_t scratch[40];
+  __shared__ uint64_t scratch[kScratch];
   __shared__ int sh_int[kShInts];
   __shared__ unsigned sh_rows;
   unsigned char* const sb = reinterpret_cast<unsigned char*>(smem);
   uint32_t* const pk = smem;                                  // [256][32]
   uint32_t* const hs = smem + u8r::kPkWords;                  // [512]
-  int32_t* const brd = reinterpret_cast<int32_t*>(hs + 512);  // [256]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
   // 16-bit shared addresses in each lane of a key register: packed bin of value
@@ -1304,11 +819,8 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
     if (threadIdx.x == 0) atomicOr(P.sticky, kErrInternal);
     return;
   }
-  // this warp's ring: kRingPairs slots of 512 bytes (lane l: 16 bytes at 16 l,
-  // two rows), then kRingPairs x 16 bytes of edge words (lane 0 at 0, lane 31 at 8)
-  const uint32_t ring_w = sbase + 4u * (uint32_t)(u8r::kBinWords + warp * u8r::kRingPairs * 132);
-  const uint32_t ring_row = ring_w + 16u * (uint32_t)lane;
-  const uint32_t ring_edge = ring_w + 512u * u8r::kRingPairs + (lane == 31 ? 8u : 0u);
+  // this warp's ring: kRingPairs slots of 512 bytes (lane l: 16 bytes at 16 l, two rows)
+  const uint32_t ring_row = sbase + 4u * (uint32_t)(u8r::kBinWords + warp * u8r::kRingPairs * 128) + 16u * (uint32_t)lane;
   auto zero_bins = [&]() {
     uint4* s4 = reinterpret_cast<uint4*>(smem);
     for (int k = threadIdx.x; k < u8r::kBinWords / 4; k += blockDim.x) s4[k] = make_uint4(0u, 0u, 0u, 0u);
@@ -1343,45 +855,46 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
         const int ya = d.y0 + ua * u8r::kUnitRows;
         const int yb = min(d.y1, d.y0 + ub * u8r::kUnitRows);
         rows_done += (uint32_t)(yb - ya);
-        const int x0 = strip * u8r::kStripPx + lane * 8;
-        const bool act = x0 < W;
+        const int x0 = strip * u8r::kStripPx + 8 * (lane - 1);
+        const bool ld_ok = x0 >= 0 && x0 < W;                    // this lane's pixels exist
+        const bool act = ld_ok && lane >= 1 && lane <= 30;       // and it owns them
         const bool lastcol = act && (x0 + 8 == W);
-        const bool need_right = act && !lastcol && lane == 31;
-        const bool need_left = act && x0 > 0 && lane == 0;
-        const bool edge_strip = (strip == 0) || ((strip + 1) * u8r::kStripPx >= W);
-        const int ylast = min(yb, H - 1);  // rows ya - 1 .. ylast are read
-        const unsigned char* rowp = d.base + (act ? x0 : 0) + (int64_t)ya * pitch;
-        const bool edge = need_right || need_left;
-        // the edge pixel: byte 0 of the word at x0 + 8, or byte 3 of the word at x0 - 4
-        const int eoff = need_right ? 8 : -4;
-        const uint32_t eshift = need_right ? 0u : 24u;
+        const uint32_t ldb = ld_ok ? 8u : 0u;                    // bytes each copy reads
+        const int ylast = min(yb, H - 1);                        // rows ya - 1 .. ylast are read
+        const unsigned char* rowp = d.base + (ld_ok ? x0 : 0) + (int64_t)ya * pitch;
+        // degree fields: 4 less the missing upper/lower neighbours; p0 at x = 0 one
+        // less, p7 of the last column one more (both ends of its padding pair)
+        const uint32_t xdeg = (x0 == 0) ? 0x00010000u : 0u;
+        const uint32_t rdeg = lastcol ? 0x00010000u : 0u;
         // row ya and the row above it: plain loads (needed at once)
         uint2 rc = make_uint2(0u, 0u);
-        uint32_t ec = 0;
-        if (act) rc = __ldg(reinterpret_cast<const uint2*>(rowp));
-        if (edge) ec = ((__ldg(reinterpret_cast<const uint32_t*>(rowp + eoff)) >> eshift) & 0xffu) << 2;
+        if (ld_ok) rc = __ldg(reinterpret_cast<const uint2*>(rowp));
         Row V = unpack_p(rc);
         if (CHECK && act) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V.E0, V.O0)), __vmaxu2(V.E1, V.O1));
         // flags [p >= u] of the pairs (upper row -> row ya); none above row 0
         uint32_t UE0 = B, UO0 = B, UE1 = B, UO1 = B;
         if (ya > 0) {
           uint2 ru = make_uint2(0u, 0u);
-          if (act) ru = __ldg(reinterpret_cast<const uint2*>(rowp - pitch));
+          if (ld_ok) ru = __ldg(reinterpret_cast<const uint2*>(rowp - pitch));
           const Row U = unpack_p(ru);
           UE0 = ge(V.E0, U.E0); UO0 = ge(V.O0, U.O0); UE1 = ge(V.E1, U.E1); UO1 = ge(V.O1, U.O1);
         }
         // rows ya + 1 .. stream through the ring in pairs: pair j holds rows
         // ya + 1 + 2 j and ya + 2 + 2 j in slot j & (kRingPairs - 1), one commit
-        // group per pair (copies past ylast are skipped)
+        // group per pair; rows past ylast are not read (their copy reads 0 bytes
+        // from the image's first row)
         const unsigned char* pf = rowp + pitch;
         int rf = ya + 1;
         uint32_t slot_w = 0;
         auto issue_pair = [&]() {
-          const uint32_t ra = ring_row + 512u * slot_w, ea = ring_edge + 16u * slot_w;
-          cp_async8(ra, pf, rf <= ylast && act);
-          cp_async4(ea, pf + eoff, rf <= ylast && edge);
-          cp_async8(ra + 8u, pf + pitch, rf + 1 <= ylast && act);
-          cp_async4(ea + 4u, pf + pitch + eoff, rf + 1 <= ylast && edge);
+          const uint32_t ra = ring_row + 512u * slot_w;
+          if (rf + 1 <= ylast) {
+            cp_async8(ra, pf, ldb);
+            cp_async8(ra + 8u, pf + pitch, ldb);
+          } else {
+            cp_async8(ra, rf <= ylast ? pf : rowp, rf <= ylast ? ldb : 0u);
+            cp_async8(ra + 8u, rowp, 0u);
+          }
           cp_commit();
           pf += 2 * pitch;
           rf += 2;
@@ -1395,23 +908,23 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
           issue_pair();                         // rows y + 2 kRingPairs - 1, y + 2 kRingPairs
           cp_wait<u8r::kRingPairs - 1>();       // rows y + 1, y + 2 have arrived
           const uint4 raw = lds128(ring_row + 512u * slot_r);
-          const uint2 ew = edge ? lds64(ring_edge + 16u * slot_r) : make_uint2(0u, 0u);
           slot_r = (slot_r + 1u) & (u8r::kRingPairs - 1);
           const Row V1 = unpack_p(make_uint2(raw.x, raw.y));
           const Row N1 = unpack_p(make_uint2(raw.z, raw.w));
-          const uint32_t ec1 = ((ew.x >> eshift) & 0xffu) << 2, ec2 = ((ew.y >> eshift) & 0xffu) << 2;
           const bool two = y + 1 < yb;          // row y + 1 belongs to the run
           const bool hd0 = y + 1 < H, hd1 = y + 2 < H;
           const uint32_t dm0 = hd0 ? B : 0u, dm1 = hd1 ? B : 0u;
+          // degree fields of the two rows (upper/lower neighbours missing at y = 0, H - 1)
+          const uint32_t DEG0 = 0x00040000u - (y == 0 ? 0x00010000u : 0u) - (hd0 ? 0u : 0x00010000u);
+          const uint32_t DEG1 = 0x00040000u - (hd1 ? 0u : 0x00010000u);
           if (CHECK && act) {
             if (two) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(V1.E0, V1.O0)), __vmaxu2(V1.E1, V1.O1));
             if (y + 2 < yb) vmax = __vmaxu2(__vmaxu2(vmax, __vmaxu2(N1.E0, N1.O0)), __vmaxu2(N1.E1, N1.O1));
           }
           // right neighbours of p7 in both rows (low half row y, high half row y + 1):
-          // p0 of the next lane, the next strip's first pixel, or (last column) p7
-          // itself, which pads the missing pair with an equal one
+          // p0 of the next lane, or (last column) p7 itself, which pads the missing
+          // pair with an equal one
           uint32_t X = __shfl_down_sync(0xffffffffu, prmt<0x5410u>(V.E0, V1.E0), 1);
-          if (need_right) X = ec | (ec1 << 16);
           if (lastcol) X = prmt<0x7632u>(V.O1, V1.O1);
           const uint32_t E0s0 = prmt<0x5432u>(V.E0, V.E1), E1s0 = prmt<0x5432u>(V.E1, X);     // (p2, p4), (p6, p8)
           const uint32_t E0s1 = prmt<0x5432u>(V1.E0, V1.E1), E1s1 = prmt<0x7632u>(V1.E1, X);
@@ -1422,10 +935,8 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
           const uint32_t DE01 = (N1.E0 + B - V1.E0) & dm1, DO01 = (N1.O0 + B - V1.O0) & dm1;
           const uint32_t DE11 = (N1.E1 + B - V1.E1) & dm1, DO11 = (N1.O1 + B - V1.O1) & dm1;
           // flags of the pairs (p-1 -> p0) in both rows: the previous lane's last
-          // right pairs, or the left strip's last pixels (value 0 at x = 0: flag 1,
-          // i.e. no contribution)
-          uint32_t Y = __shfl_up_sync(0xffffffffu, prmt<0x7632u>(GO10, GO11), 1);
-          if (lane == 0) Y = ge(prmt<0x5410u>(V.E0, V1.E0), need_left ? (ec | (ec1 << 16)) : 0u);
+          // right pairs (a context lane left of the image holds zeros: flag 1)
+          const uint32_t Y = __shfl_up_sync(0xffffffffu, prmt<0x7632u>(GO10, GO11), 1);
           const uint32_t LE00 = prmt<0x5410u>(Y, GO00), LE10 = prmt<0x5432u>(GO00, GO10);  // pairs ending at p0, p2 / p4, p6
           const uint32_t LE01 = prmt<0x5432u>(Y, GO01), LE11 = prmt<0x5432u>(GO01, GO11);
           // n_lo * 1024 per pixel: [right >= p] + [lower >= p] + [left > p] + [upper > p]
@@ -1438,32 +949,18 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
           const uint32_t nE11 = (GE11 + DE11 + 2 * B) - (LE11 + DE10);
           const uint32_t nO11 = (GO11 + DO11 + 2 * B) - (GE11 + DO10);
           if (act) {
-            u8r_row_updates(V, V1, E0s0, E1s0, nE00, nO00, nE10, nO10, PK2, HS2, hd0);
-            if (two) u8r_row_updates(V1, N1, E0s1, E1s1, nE01, nO01, nE11, nO11, PK2, HS2, hd1);
-            // border deficits 4 - deg(p); the padded right pair of the last column
-            // counts -1 (its partner is absent)
-            if (y == 0 || !hd0) u8r_row_border(brd, V, (y == 0 ? 1 : 0) + (hd0 ? 0 : 1));
-            if (two && !hd1) u8r_row_border(brd, V1, 1);
-            if (edge_strip) {
-              if (x0 == 0) {
-                atomicAdd(&brd[(V.E0 & 0xffffu) >> 2], 1);
-                if (two) atomicAdd(&brd[(V1.E0 & 0xffffu) >> 2], 1);
-              }
-              if (lastcol) {
-                atomicAdd(&brd[V.O1 >> 18], -1);
-                if (two) atomicAdd(&brd[V1.O1 >> 18], -1);
-              }
-            }
+            u8r_row_updates(V, V1, E0s0, E1s0, nE00, nO00, nE10, nO10, DEG0, DEG0 - xdeg, DEG0 + rdeg, PK2, HS2, hd0);
+            if (two)
+              u8r_row_updates(V1, N1, E0s1, E1s1, nE01, nO01, nE11, nO11, DEG1, DEG1 - xdeg, DEG1 + rdeg, PK2, HS2, hd1);
           }
           V = N1;
-          ec = ec2;
           UE0 = DE01; UO0 = DO01; UE1 = DE11; UO1 = DO11;
         }
       }
       if (lane == 0 && rows_done) atomicAdd(&sh_rows, rows_done);
       wait_prior();
       __syncthreads();
-      u8r_fold_flush(P, i, pk, hs, brd);
+      u8r_fold_flush(P, i, pk, hs);
       __syncthreads();
     }
     if (CHECK && ((vmax & 0xffffu) > lastv4 || (vmax >> 16) > lastv4)) atomicOr(P.err + d.slot, kErrRange);
@@ -1485,7 +982,7 @@ __global__ void __launch_bounds__(u8r::kNW * 32, 1) k_u8r(const __grid_constant_
 template <int ELEM, bool GLOBAL>
 __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
-  __shared__ uint64_t scratch[40];
+  __shared__ uint64_t scratch[kScratch];
   __shared__ int sh_int[kShInts];
   constexpr int NW = 8;
   const int bins = P.bins;
@@ -1596,7 +1093,7 @@ struct ThreshParams {
 // (2 M uint64 + candidates).
 __global__ void __launch_bounds__(kEpiThreads) k_thresholds(const __grid_constant__ ThreshParams Q) {
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ uint64_t scratch[40];
+  __shared__ uint64_t scratch[kScratch];
   __shared__ int sh_int[kShInts];
   const int i = blockIdx.x;
   const uint64_t* card = Q.card + (size_t)i * Q.M;
