@@ -106,12 +106,14 @@ int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, i
                          int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
                          int32_t* out_count, int32_t* out_t0, void* cuda_stream);
 
-/* Whole path from HOST memory and back, synchronously: the image is copied to the
- * device in row bands on a copy stream while earlier bands are already being
- * reduced, then card/sumc/curve and the thresholds are copied back.
- * img: host pointer (pinned memory gives the fastest copies); outputs: HOST
- * arrays card/sumc uint64[M], curve double[M], out_t int32[max_k] (any output
- * may be NULL).  Returns KOHLER_ERR_RANGE directly for a pixel >= M. */
+/* Whole path from HOST memory and back, synchronously.  A pinned (page-locked,
+ * device-mapped) image is read by the kernel itself over the host link, with no
+ * staging copy; any other image is copied to the device in row bands on a copy
+ * stream while earlier bands are already being reduced.  Then card/sumc/curve
+ * and the thresholds are copied back.
+ * img: host pointer; outputs: HOST arrays card/sumc uint64[M], curve double[M],
+ * out_t int32[max_k] (any output may be NULL).  Returns KOHLER_ERR_RANGE directly
+ * for a pixel >= M. */
 int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
                         int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc,
                         double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0);
@@ -138,7 +140,8 @@ int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int6
  * a pixel >= M, KOHLER_ERR_CUDA on a CUDA error, else KOHLER_OK. */
 int kohler_stream_status(void* cuda_stream);
 
-/* Frees the workspaces of the current device (all streams).  Only call when no
+/* Frees the workspaces of the current device (all streams) and the buffers of
+ * kohler_analyze_host on it.  Only call when no
  * work of this library is in flight on the device. */
 int kohler_release(void);
 

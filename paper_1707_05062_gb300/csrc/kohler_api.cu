@@ -457,6 +457,10 @@ int kohler_stream_status(void* cuda_stream) {
   return (bits & kErrRange) ? KOHLER_ERR_RANGE : KOHLER_OK;
 }
 
+namespace {
+void release_host_path(int dev);
+}  // namespace
+
 int kohler_release(void) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -471,6 +475,7 @@ int kohler_release(void) {
       ++it;
     }
   }
+  release_host_path(dev);
   return KOHLER_OK;
 }
 
@@ -498,10 +503,29 @@ struct HostPath {
   size_t dimg_bytes = 0;
   void* dout = nullptr;
   size_t dout_bytes = 0;
+  void* hout = nullptr;  // pinned mirror of dout
   std::vector<cudaEvent_t> ev;
 };
 std::mutex g_host_mu;
 std::map<int, HostPath*> g_host;
+
+// Frees the host path of a device (streams, buffers, events).
+void release_host_path(int dev) {
+  std::lock_guard<std::mutex> lock(g_host_mu);
+  auto it = g_host.find(dev);
+  if (it == g_host.end()) return;
+  HostPath* h = it->second;
+  if (h->compute) cudaStreamSynchronize(h->compute);
+  if (h->copy) cudaStreamSynchronize(h->copy);
+  if (h->dimg) cudaFree(h->dimg);
+  if (h->dout) cudaFree(h->dout);
+  if (h->hout) cudaFreeHost(h->hout);
+  for (cudaEvent_t x : h->ev) cudaEventDestroy(x);
+  if (h->compute) cudaStreamDestroy(h->compute);
+  if (h->copy) cudaStreamDestroy(h->copy);
+  delete h;
+  g_host.erase(it);
+}
 
 int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
   int dev = 0;
@@ -523,9 +547,11 @@ int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
   }
   if (h->dout_bytes < out_bytes) {
     if (h->dout) cudaFree(h->dout);
-    h->dout = nullptr;
+    if (h->hout) cudaFreeHost(h->hout);
+    h->dout = h->hout = nullptr;
     h->dout_bytes = 0;
     if ((e = cudaMalloc(&h->dout, out_bytes)) != cudaSuccess) return status_of(e);
+    if ((e = cudaHostAlloc(&h->hout, out_bytes, cudaHostAllocDefault)) != cudaSuccess) return status_of(e);
     h->dout_bytes = out_bytes;
   }
   while ((int)h->ev.size() < bands) {
@@ -547,60 +573,84 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   rc = check_image(img, dt, width, height, pitch_bytes);
   if (rc) return rc;
   const int es = dt == KOHLER_U8 ? 1 : 2;
-  const int64_t dpitch = ((width * es + 127) / 128) * 128;  // device rows: aligned for the fast pass
-  const size_t img_bytes = (size_t)dpitch * height;
   // device outputs: card, sumc (uint64 M), curve (double M), out_t (max_k), count, t0
   const size_t o_card = 0, o_sumc = (size_t)M * 8, o_curve = 2 * (size_t)M * 8, o_t = 3 * (size_t)M * 8;
   const size_t o_cnt = o_t + ((size_t)std::max(max_k, 1) * 4 + 15) / 16 * 16, o_t0 = o_cnt + 16;
   const size_t out_bytes = o_t0 + 16;
+  // Pinned (or otherwise device-mapped) host memory is read by the pass itself,
+  // over the host link, with no staging copy; other memory is copied in bands.
+  cudaPointerAttributes pa;
+  const void* mapped = nullptr;
+  if (cudaPointerGetAttributes(&pa, img) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
+  } else {
+    cudaGetLastError();  // an unknown pointer is ordinary pageable memory
+  }
+  // packed rows are copied as they are (one contiguous copy per band); others go
+  // to rows padded to 128 bytes
+  const bool packed = pitch_bytes == width * es && (width * es) % 8 == 0;
+  const int64_t dpitch = packed ? width * es : ((width * es + 127) / 128) * 128;
+  const size_t img_bytes = mapped ? 0 : (size_t)dpitch * height;
   // bands of rows: copy band b + 1 while band b is reduced (a band needs the first
   // row of the next band for its lower pairs)
-  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
+  const int nbands = mapped ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
   std::lock_guard<std::mutex> lock(g_host_mu);
   HostPath* h = nullptr;
   rc = host_path(&h, img_bytes, out_bytes, nbands + 1);
   if (rc) return rc;
-  char* dimg = static_cast<char*>(h->dimg);
   char* dout = static_cast<char*>(h->dout);
-  // band edges on multiples of 8 rows (the uint8 pass works on 8-row tiles)
-  std::vector<int32_t> yb(nbands + 1);
-  for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)std::min<int64_t>(height, ((height * b) / nbands + 7) / 8 * 8);
-  yb[nbands] = (int32_t)height;
+  auto reduce = [&](const kohler_image& im, const std::vector<Band>* band) {
+    return run_batch(&im, 1, dt, M, max_k, reinterpret_cast<uint64_t*>(dout + o_card),
+                     reinterpret_cast<uint64_t*>(dout + o_sumc), reinterpret_cast<double*>(dout + o_curve),
+                     max_k > 0 ? reinterpret_cast<int32_t*>(dout + o_t) : nullptr,
+                     reinterpret_cast<int32_t*>(dout + o_cnt), reinterpret_cast<int32_t*>(dout + o_t0), h->compute,
+                     band);
+  };
   cudaError_t e = cudaSuccess;
-  for (int b = 0; b < nbands && e == cudaSuccess; ++b) {
-    const int64_t r0 = yb[b], r1 = yb[b + 1];
-    if (r1 > r0)
-      e = cudaMemcpy2DAsync(dimg + r0 * dpitch, dpitch, static_cast<const char*>(img) + r0 * pitch_bytes, pitch_bytes,
-                            width * es, r1 - r0, cudaMemcpyHostToDevice, h->copy);
-    if (e == cudaSuccess) e = cudaEventRecord(h->ev[b], h->copy);
-  }
-  if (e != cudaSuccess) return status_of(e);
-  kohler_image im{dimg, width, height, dpitch};
-  for (int b = 0; b < nbands; ++b) {
-    // band b reads rows [yb[b] - 1, yb[b + 1]]: wait for its own copy and the next one
-    e = cudaStreamWaitEvent(h->compute, h->ev[std::min(b + 1, nbands - 1)], 0);
-    if (e != cudaSuccess) return status_of(e);
-    std::vector<Band> band(1, Band{yb[b], yb[b + 1]});
-    if (yb[b + 1] <= yb[b]) continue;
-    rc = run_batch(&im, 1, dt, M, max_k, reinterpret_cast<uint64_t*>(dout + o_card),
-                   reinterpret_cast<uint64_t*>(dout + o_sumc), reinterpret_cast<double*>(dout + o_curve),
-                   max_k > 0 ? reinterpret_cast<int32_t*>(dout + o_t) : nullptr,
-                   reinterpret_cast<int32_t*>(dout + o_cnt), reinterpret_cast<int32_t*>(dout + o_t0), h->compute,
-                   &band);
+  if (mapped) {
+    rc = reduce(kohler_image{mapped, width, height, pitch_bytes}, nullptr);
     if (rc) return rc;
+  } else {
+    char* dimg = static_cast<char*>(h->dimg);
+    // band edges on multiples of 8 rows
+    std::vector<int32_t> yb(nbands + 1);
+    for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)std::min<int64_t>(height, ((height * b) / nbands + 7) / 8 * 8);
+    yb[nbands] = (int32_t)height;
+    for (int b = 0; b < nbands && e == cudaSuccess; ++b) {
+      const int64_t r0 = yb[b], r1 = yb[b + 1];
+      if (r1 > r0) {
+        const char* src = static_cast<const char*>(img) + r0 * pitch_bytes;
+        e = packed ? cudaMemcpyAsync(dimg + r0 * dpitch, src, (size_t)(r1 - r0) * dpitch, cudaMemcpyHostToDevice, h->copy)
+                   : cudaMemcpy2DAsync(dimg + r0 * dpitch, dpitch, src, pitch_bytes, width * es, r1 - r0,
+                                       cudaMemcpyHostToDevice, h->copy);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(h->ev[b], h->copy);
+    }
+    if (e != cudaSuccess) return status_of(e);
+    const kohler_image im{dimg, width, height, dpitch};
+    for (int b = 0; b < nbands; ++b) {
+      // band b reads rows [yb[b] - 1, yb[b + 1]]: wait for its own copy and the next one
+      e = cudaStreamWaitEvent(h->compute, h->ev[std::min(b + 1, nbands - 1)], 0);
+      if (e != cudaSuccess) return status_of(e);
+      if (yb[b + 1] <= yb[b]) continue;
+      std::vector<Band> band(1, Band{yb[b], yb[b + 1]});
+      rc = reduce(im, &band);
+      if (rc) return rc;
+    }
   }
-  // results back to the host
+  // results back to the host: one copy into the pinned mirror, then host copies
+  e = cudaMemcpyAsync(h->hout, dout, out_bytes, cudaMemcpyDeviceToHost, h->compute);
+  if (e != cudaSuccess) return status_of(e);
+  rc = kohler_stream_status(h->compute);  // waits for the stream
+  if (rc != KOHLER_OK && rc != KOHLER_ERR_RANGE) return rc;
+  const char* ho = static_cast<const char*>(h->hout);
   struct Cp {
     void* dst;
     size_t off, bytes;
   } cps[] = {{card, o_card, (size_t)M * 8},   {sumc, o_sumc, (size_t)M * 8}, {curve, o_curve, (size_t)M * 8},
              {out_t, o_t, (size_t)max_k * 4}, {out_count, o_cnt, 4},          {out_t0, o_t0, 4}};
-  for (auto& c : cps) {
-    if (!c.dst || c.bytes == 0) continue;
-    e = cudaMemcpyAsync(c.dst, dout + c.off, c.bytes, cudaMemcpyDeviceToHost, h->compute);
-    if (e != cudaSuccess) return status_of(e);
-  }
-  rc = kohler_stream_status(h->compute);
+  for (auto& c : cps)
+    if (c.dst && c.bytes) memcpy(c.dst, ho + c.off, c.bytes);
   return rc;
 }
 

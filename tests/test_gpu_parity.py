@@ -315,6 +315,15 @@ def test_analyze_host(shape):
     assert_same(got, expect(img, 256))
 
 
+@pytest.mark.parametrize("dtype,w,h,M", [(np.uint8, 1000, 600, 256), (np.uint8, 333, 101, 200), (np.uint16, 516, 130, 4096)])
+def test_analyze_host_pinned(dtype, w, h, M):
+    # pinned host memory is read by the kernel directly (no staging copy)
+    img = synth.smooth_image(91, w, h, M, dtype)
+    src = torch.from_numpy(img.view(np.int16) if dtype == np.uint16 else img).pin_memory()
+    got = K().analyze_host(src, M, MAX_K)
+    assert_same((got[0], got[1], got[2], got[3], got[4], got[5]), expect(img, M), f"pinned {w}x{h}")
+
+
 def test_analyze_host_u16_and_range():
     k = K()
     img = synth.smooth_image(8, 200, 150, 4096, np.uint16, noise_sd=25.0)
