@@ -578,19 +578,26 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
         def producer():
             for j, (r, k) in enumerate(order):
                 if times is not None:
-                    dt = t_base + times[j] - time.perf_counter()
-                    if dt > 0:
-                        time.sleep(dt)
+                    # sleep until shortly before the arrival, then spin: a plain
+                    # sleep overshoots by tens of microseconds
+                    target = t_base + times[j]
+                    dt = target - time.perf_counter()
+                    if dt > 3e-4:
+                        time.sleep(dt - 3e-4)
+                    while time.perf_counter() < target:
+                        pass
                 t_arr = t_base + times[j] if times is not None else time.perf_counter()
-                q.put((j, srv.submit(frames[r][k]), t_arr))
+                t_sub = time.perf_counter()
+                q.put((j, srv.submit(frames[r][k]), t_arr, t_sub))
 
         th = threading.Thread(target=producer)
         t_start = time.perf_counter()
         th.start()
         for _ in range(len(order)):
-            j, ticket, t_arr = q.get()
+            j, ticket, t_arr, t_sub = q.get()
             t0, cnt, ts, lat_srv = srv.poll(ticket)
-            results[j] = (t0, cnt, ts, time.perf_counter() - t_arr, lat_srv)
+            t_done = time.perf_counter()
+            results[j] = (t0, cnt, ts, t_done - t_arr, lat_srv, t_done - t_sub, t_sub - t_arr)
         th.join()
         t_end = time.perf_counter()
         stats = srv.stats()
@@ -604,10 +611,16 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
     ok = ok and all((r[0], r[1], r[2]) == want[s] for r, s in zip(results, src))
     out["open_loop"] = {"fps_achieved": n_frames / (t_b - t_a), "latency_ms_p50": _pct(lat, 50) * 1e3,
                         "latency_ms_p99": _pct(lat, 99) * 1e3, "latency_ms_max": max(lat) * 1e3,
+                        "submit_to_result_ms_p50": _pct([r[5] for r in results], 50) * 1e3,
+                        "submit_to_result_ms_p99": _pct([r[5] for r in results], 99) * 1e3,
+                        "producer_lateness_ms_p99": _pct([r[6] for r in results], 99) * 1e3,
                         "server_latency_ms_p50": _pct([r[4] for r in results], 50) * 1e3,
                         "server_latency_ms_p99": _pct([r[4] for r in results], 99) * 1e3,
                         "launches": stats[2], "max_frames_per_launch": stats[3],
-                        "latency": "scheduled arrival -> thresholds in host memory"}
+                        "latency": "scheduled arrival -> thresholds in host memory (poll returned)",
+                        "by_resolution": {f"{w}x{h}": {"p50_ms": _pct([x[3] for x, (r, _) in zip(results, src) if r == ri], 50) * 1e3,
+                                                       "p99_ms": _pct([x[3] for x, (r, _) in zip(results, src) if r == ri], 99) * 1e3}
+                                          for ri, (w, h) in enumerate(synth.VIDEO_SIZES)}}
     # (ii) closed loop: every frame submitted as soon as the staging queue takes it
     sub = src[:closed_frames]
     results, t_a, t_b, stats = run(sub, None)

@@ -96,6 +96,8 @@ struct kohler_server {
   std::thread worker;
 
   void run();
+  bool launch_ready();       // (mu held) one fused launch per dtype over the frames whose copy is done
+  void retire(LaunchRec& L);  // (mu held) results of a finished launch to its frames
   cudaEvent_t get_event();
   void put_event(cudaEvent_t e) { event_pool.push_back(e); }
   void* dev_alloc(size_t bytes);
@@ -167,6 +169,109 @@ void* kohler_server::host_alloc(size_t bytes) {
   return p;
 }
 
+// One fused launch per dtype over every admitted frame whose copy has completed
+// (up to 64), with the copies of its results to the pinned mirrors and a done
+// event.  Called with `mu` held, by the scheduler thread or by kohler_submit.
+bool kohler_server::launch_ready() {
+  std::vector<Frame*> ready;
+  for (auto it = copying.begin(); it != copying.end() && ready.size() < 64;) {
+    Frame* f = *it;
+    if (!f->copied || cudaEventQuery(f->copied) == cudaSuccess) {
+      ready.push_back(f);
+      if (f->copied) put_event(f->copied);
+      f->copied = nullptr;
+      it = copying.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  if (!ready.empty()) {
+    // one launch per dtype present
+    for (int dtc = 1; dtc <= 2; ++dtc) {
+      std::vector<kohler_image> imgs;
+      std::vector<int> outs;
+      std::vector<Frame*> fr;
+      for (Frame* f : ready)
+        if ((int)f->dt == dtc) {
+          imgs.push_back(kohler_image{f->dev, f->W, f->H, f->dpitch});
+          outs.push_back(f->slot);
+          fr.push_back(f);
+        }
+      if (fr.empty()) continue;
+      kohler::OutSpec o{d_card, d_sumc, d_curve, max_k > 0 ? d_t : nullptr, d_cnt, d_t0, d_status, max_k};
+      int rc = kohler::launch_images(imgs.data(), (int)imgs.size(), (kohler_dtype)dtc, M, outs.data(), o, compute);
+      cudaError_t e = cudaSuccess;
+      for (size_t j = 0; rc == KOHLER_OK && j < fr.size() && e == cudaSuccess; ++j) {
+        const int s = fr[j]->slot;
+        if (max_k > 0)
+          e = cudaMemcpyAsync(h_t + (size_t)s * max_k, d_t + (size_t)s * max_k, sizeof(int32_t) * max_k,
+                              cudaMemcpyDeviceToHost, compute);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt + s, d_cnt + s, 4, cudaMemcpyDeviceToHost, compute);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_t0 + s, d_t0 + s, 4, cudaMemcpyDeviceToHost, compute);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_status + s, d_status + s, 4, cudaMemcpyDeviceToHost, compute);
+      }
+      LaunchRec rec;
+      rec.done = get_event();
+      if (rc == KOHLER_OK && e == cudaSuccess && rec.done) e = cudaEventRecord(rec.done, compute);
+      if (rc != KOHLER_OK || e != cudaSuccess || !rec.done) {
+        const int st = rc != KOHLER_OK ? rc : (e != cudaSuccess ? status_of(e) : KOHLER_ERR_CUDA);
+        for (Frame* f : fr) {
+          f->status = st;
+          f->state = FrameState::Done;
+          ++n_finished;
+        }
+        if (rec.done) put_event(rec.done);
+        cv_done.notify_all();
+        continue;
+      }
+      rec.frames = fr;
+      rec.active = true;
+      int li = -1;
+      for (size_t k = 0; k < launches.size(); ++k)
+        if (!launches[k].active) { li = (int)k; break; }
+      if (li < 0) {
+        launches.push_back(rec);
+        li = (int)launches.size() - 1;
+      } else {
+        launches[li] = rec;
+      }
+      for (Frame* f : fr) {
+        f->state = FrameState::Running;
+        f->launch = li;
+      }
+      cv_done.notify_all();  // pollers of these frames now wait on the launch's event
+      running += (int)fr.size();
+      ++n_launches;
+      max_per_launch = std::max<uint64_t>(max_per_launch, fr.size());
+    }
+  }
+  return !ready.empty();
+}
+
+// Results of a finished launch to its frames (called with `mu` held).
+void kohler_server::retire(LaunchRec& L) {
+  if (!L.active) return;
+  const auto now = Clock::now();
+  for (Frame* f : L.frames) {
+    const int s = f->slot;
+    f->t0 = h_t0[s];
+    f->count = h_cnt[s];
+    f->status = h_status[s] == KOHLER_ERR_RANGE ? KOHLER_ERR_RANGE : KOHLER_OK;
+    if (max_k > 0) f->ts.assign(h_t + (size_t)s * max_k, h_t + (size_t)(s + 1) * max_k);
+    f->latency_s = std::chrono::duration<double>(now - f->t_submit).count();
+    f->state = FrameState::Done;
+    dev_release(f->dev, f->bytes);  // the frame's pixels are no longer needed
+    f->dev = nullptr;
+    ++n_finished;
+    --running;
+  }
+  put_event(L.done);
+  L.done = nullptr;
+  L.frames.clear();
+  L.active = false;
+  cv_done.notify_all();
+}
+
 // Scheduler loop.  Each pass: (1) admit queued frames (slot + device memory) and
 // start their copies; (2) launch one fused reduction over every admitted frame
 // whose copy has finished; (3) retire finished launches.  Spins while GPU work is
@@ -214,100 +319,11 @@ void kohler_server::run() {
       progressed = true;
     }
     // (2) one launch over the frames whose copies are complete
-    std::vector<Frame*> ready;
-    for (auto it = copying.begin(); it != copying.end() && ready.size() < 64;) {
-      Frame* f = *it;
-      if (!f->copied || cudaEventQuery(f->copied) == cudaSuccess) {
-        ready.push_back(f);
-        if (f->copied) put_event(f->copied);
-        f->copied = nullptr;
-        it = copying.erase(it);
-      } else {
-        ++it;
-      }
-    }
-    if (!ready.empty()) {
-      // one launch per dtype present
-      for (int dtc = 1; dtc <= 2; ++dtc) {
-        std::vector<kohler_image> imgs;
-        std::vector<int> outs;
-        std::vector<Frame*> fr;
-        for (Frame* f : ready)
-          if ((int)f->dt == dtc) {
-            imgs.push_back(kohler_image{f->dev, f->W, f->H, f->dpitch});
-            outs.push_back(f->slot);
-            fr.push_back(f);
-          }
-        if (fr.empty()) continue;
-        kohler::OutSpec o{d_card, d_sumc, d_curve, max_k > 0 ? d_t : nullptr, d_cnt, d_t0, d_status, max_k};
-        int rc = kohler::launch_images(imgs.data(), (int)imgs.size(), (kohler_dtype)dtc, M, outs.data(), o, compute);
-        cudaError_t e = cudaSuccess;
-        for (size_t j = 0; rc == KOHLER_OK && j < fr.size() && e == cudaSuccess; ++j) {
-          const int s = fr[j]->slot;
-          if (max_k > 0)
-            e = cudaMemcpyAsync(h_t + (size_t)s * max_k, d_t + (size_t)s * max_k, sizeof(int32_t) * max_k,
-                                cudaMemcpyDeviceToHost, compute);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt + s, d_cnt + s, 4, cudaMemcpyDeviceToHost, compute);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(h_t0 + s, d_t0 + s, 4, cudaMemcpyDeviceToHost, compute);
-          if (e == cudaSuccess) e = cudaMemcpyAsync(h_status + s, d_status + s, 4, cudaMemcpyDeviceToHost, compute);
-        }
-        LaunchRec rec;
-        rec.done = get_event();
-        if (rc == KOHLER_OK && e == cudaSuccess && rec.done) e = cudaEventRecord(rec.done, compute);
-        if (rc != KOHLER_OK || e != cudaSuccess || !rec.done) {
-          const int st = rc != KOHLER_OK ? rc : (e != cudaSuccess ? status_of(e) : KOHLER_ERR_CUDA);
-          for (Frame* f : fr) {
-            f->status = st;
-            f->state = FrameState::Done;
-            ++n_finished;
-          }
-          if (rec.done) put_event(rec.done);
-          cv_done.notify_all();
-          continue;
-        }
-        rec.frames = fr;
-        rec.active = true;
-        int li = -1;
-        for (size_t k = 0; k < launches.size(); ++k)
-          if (!launches[k].active) { li = (int)k; break; }
-        if (li < 0) {
-          launches.push_back(rec);
-          li = (int)launches.size() - 1;
-        } else {
-          launches[li] = rec;
-        }
-        for (Frame* f : fr) {
-          f->state = FrameState::Running;
-          f->launch = li;
-        }
-        running += (int)fr.size();
-        ++n_launches;
-        max_per_launch = std::max<uint64_t>(max_per_launch, fr.size());
-      }
-      progressed = true;
-    }
+    if (launch_ready()) progressed = true;
     // (3) retire finished launches
     for (auto& L : launches) {
       if (!L.active || cudaEventQuery(L.done) != cudaSuccess) continue;
-      const auto now = Clock::now();
-      for (Frame* f : L.frames) {
-        const int s = f->slot;
-        f->t0 = h_t0[s];
-        f->count = h_cnt[s];
-        f->status = h_status[s] == KOHLER_ERR_RANGE ? KOHLER_ERR_RANGE : KOHLER_OK;
-        if (max_k > 0) f->ts.assign(h_t + (size_t)s * max_k, h_t + (size_t)(s + 1) * max_k);
-        f->latency_s = std::chrono::duration<double>(now - f->t_submit).count();
-        f->state = FrameState::Done;
-        dev_release(f->dev, f->bytes);  // the frame's pixels are no longer needed
-        f->dev = nullptr;
-        ++n_finished;
-        --running;
-      }
-      put_event(L.done);
-      L.done = nullptr;
-      L.frames.clear();
-      L.active = false;
-      cv_done.notify_all();
+      retire(L);
       progressed = true;
     }
     const bool busy = !copying.empty() || running > 0;
@@ -374,6 +390,15 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
   const int es = dt == KOHLER_U8 ? 1 : 2;
   if (width < 1 || height < 1 || pitch_bytes < width * es || width > (1 << 30) || height > (1 << 30))
     return KOHLER_ERR_ARG;
+  int prev_dev = 0;
+  cudaGetDevice(&prev_dev);
+  if (prev_dev != s->device) cudaSetDevice(s->device);
+  struct Restore {
+    int dev, cur;
+    ~Restore() {
+      if (dev != cur) cudaSetDevice(dev);
+    }
+  } restore{prev_dev, s->device};
   Frame* f = new Frame();
   f->dt = dt;
   f->W = width;
@@ -433,6 +458,9 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
       return KOHLER_OK;  // the error is reported by kohler_poll
     }
     s->copying.push_back(f);  // copy complete: no event (f->copied stays null)
+    // launch now (with any other frame whose copy is done) rather than wake the
+    // scheduler thread: one thread hand-off less per frame
+    s->launch_ready();
   } else {
     // copy into pinned staging (compact rows); the scheduler admits it later
     const char* src = static_cast<const char*>(host_frame);
@@ -460,11 +488,37 @@ int kohler_poll(kohler_server* s, uint64_t ticket, kohler_result* out, int64_t t
   if (it == s->frames.end()) return KOHLER_ERR_ARG;
   Frame* f = it->second;
   auto done = [&] { return f->state == FrameState::Done; };
-  if (!done()) {
-    if (timeout_us == 0) return KOHLER_PENDING;
+  const auto deadline = Clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+  if (!done() && timeout_us == 0) {
+    // the frame's launch may have finished without being retired yet
+    if (f->state == FrameState::Running && cudaEventQuery(s->launches[f->launch].done) == cudaSuccess)
+      s->retire(s->launches[f->launch]);
+    if (!done()) return KOHLER_PENDING;
+  }
+  while (!done()) {
+    if (f->state == FrameState::Running) {
+      // wait for the frame's own launch and retire it here (no hand-off to the
+      // scheduler thread); while f is Running its launch record is not reused
+      const cudaEvent_t ev = s->launches[f->launch].done;
+      lk.unlock();
+      bool finished = false;
+      while (true) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaSuccess) { finished = true; break; }
+        if (q != cudaErrorNotReady) break;  // a CUDA error: leave it to the scheduler thread
+        if (timeout_us > 0 && Clock::now() >= deadline) break;
+        std::this_thread::yield();
+      }
+      lk.lock();
+      if (finished && f->state == FrameState::Running) s->retire(s->launches[f->launch]);
+      if (done()) break;
+      if (timeout_us > 0 && Clock::now() >= deadline) return KOHLER_ERR_TIMEOUT;
+      if (!finished) s->cv_done.wait_for(lk, std::chrono::microseconds(200));
+      continue;
+    }
     if (timeout_us < 0) {
-      s->cv_done.wait(lk, done);
-    } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {
+      s->cv_done.wait(lk, [&] { return done() || f->state == FrameState::Running; });
+    } else if (!s->cv_done.wait_until(lk, deadline, [&] { return done() || f->state == FrameState::Running; })) {
       return KOHLER_ERR_TIMEOUT;
     }
   }
