@@ -121,7 +121,7 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
 /* kohler_analyze_batch for one device image, without any device allocation (the
  * paper has no counterpart; this serves callers that cannot allocate while they
  * run, e.g. inside a real-time loop or under a fixed memory budget).  Scratch
- * lives in a fixed 144 KiB array in device memory that every GPU which loads the
+ * lives in a fixed 148 KiB array in device memory that every GPU which loads the
  * library keeps until the process exits; M is limited to 4096 (KOHLER_ERR_ARG
  * above).  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress): make that first call before capturing the stream

@@ -170,7 +170,7 @@ KernelInfo kernel_for(Pass p, int bins) {
 // curves and threshold candidates, plus the histograms when the whole set fits
 // below 100 KB (the block's own pass needs `pass_smem`).
 size_t epilogue_smem(int M, int bins, size_t pass_smem) {
-  const size_t cs = (size_t)2 * M * 8 + (((size_t)(M + 1) / 2 + 2) * 4 + 15) / 16 * 16;
+  const size_t cs = (size_t)2 * M * 8 + ((size_t)cand_ints(M) * 4 + 15) / 16 * 16;
   const size_t full = cs + (size_t)4 * bins * 8;
   const size_t cap = 100 * 1024;
   if (full <= cap) return full;
@@ -301,7 +301,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
               cudaStream_t stream, const std::vector<Band>* bands, const int* out_index = nullptr,
               int32_t* out_status = nullptr) {
   const int bins = bins_for(dt, M);
-  const int cand_stride = (M + 1) / 2 + 2;
+  const int cand_stride = cand_ints(M);
   const int chunk = std::min<int>(kMaxBatch, std::max<int>(1, (int)std::min<int64_t>(
                                                                kMaxBatch, ((int64_t)256 << 20) / ((int64_t)bins * 32))));
   Workspace* ws = nullptr;
@@ -404,7 +404,7 @@ int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int
   if (n == 0) return KOHLER_OK;
   if (!card || !sumc || !out_count || !out_t0 || (max_k > 0 && !out_t)) return KOHLER_ERR_ARG;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
-  const int cand_stride = (M + 1) / 2 + 2;
+  const int cand_stride = cand_ints(M);
   Workspace* ws = nullptr;
   int rc = get_workspace(stream, kMaxBatch, 32, cand_stride, &ws);
   if (rc) return rc;
@@ -421,7 +421,7 @@ int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int
     Q.cand = ws->cand;
     Q.cand_stride = ws->cand_stride;
     const size_t smem = epilogue_smem(M, 32, 0);
-    const size_t cs = (size_t)2 * M * 8 + (((size_t)(M + 1) / 2 + 2) * 4 + 15) / 16 * 16;
+    const size_t cs = (size_t)2 * M * 8 + ((size_t)cand_ints(M) * 4 + 15) / 16 * 16;
     Q.staged = smem >= cs ? 1 : 0;
     const size_t dyn = Q.staged ? cs : 0;
     if (dyn > 48 * 1024) cudaFuncSetAttribute((const void*)k_thresholds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -665,7 +665,7 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
 // exits.
 namespace {
 
-constexpr size_t kNoAllocScratchBytes = 144 * 1024;
+constexpr size_t kNoAllocScratchBytes = 148 * 1024;
 constexpr int kNoAllocMaxM = 4096;  // 4 bins * 4096 * 8 B of histograms + candidates fit
 
 // Laid out as: histograms (4 * bins uint64), then at kCountersAt the image's
@@ -674,7 +674,7 @@ constexpr int kNoAllocMaxM = 4096;  // 4 bins * 4096 * 8 B of histograms + candi
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 constexpr size_t kCountersAt = (size_t)4 * kNoAllocMaxM * 8;      // 131072
 constexpr size_t kCandAt = kCountersAt + 256;
-static_assert(kCandAt + ((size_t)(kNoAllocMaxM + 1) / 2 + 2) * 4 <= kNoAllocScratchBytes, "scratch too small");
+static_assert(kCandAt + (size_t)cand_ints(kNoAllocMaxM) * 4 <= kNoAllocScratchBytes, "scratch too small");
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal (set up once)
@@ -737,7 +737,7 @@ extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t 
   base.err = reinterpret_cast<unsigned*>(s + kCountersAt + 4);
   base.sticky = reinterpret_cast<unsigned*>(s + kCountersAt + 8);
   base.cand = reinterpret_cast<int32_t*>(s + kCandAt);
-  base.cand_stride = (M + 1) / 2 + 2;
+  base.cand_stride = cand_ints(M);
   std::vector<int> idx(1, 0), slot_of(1, 0);
   return launch_group(pass, idx, &im, nullptr, M, bins, nullptr, base, stream, slot_of, nullptr);
 }

@@ -37,6 +37,10 @@ constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
 constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, warp winners, per-warp top lists
 constexpr int kScratch = 3 * 33;       // shared uint64 scratch of a block (block scans of up to 3 values)
 
+// Ints of threshold-candidate scratch for M levels: up to (M + 1) / 2 + 1
+// candidates, each with its t and the float of its C.
+__host__ __device__ constexpr int cand_ints(int M) { return 2 * ((M + 1) / 2 + 2); }
+
 enum ErrBits : unsigned { kErrRange = 1u, kErrInternal = 2u };
 
 struct ImgDesc {
@@ -173,11 +177,14 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
   const int c0 = min(M, (int)threadIdx.x * chunk), c1 = min(M, c0 + chunk);
   const int S = 2 * M - 1;  // s in [0, 2M - 2]
   // pass 1: chunk sums of H_lo, H_hi, and of H_s over u in [2 c0, 2 c1)
+  // (loops unrolled so that the independent loads of a chunk are in flight together)
   uint64_t sl = 0, sh = 0, ss = 0;
+#pragma unroll 8
   for (int t = c0; t < c1; ++t) {
     sl += ldh<H_GLOBAL>(hlo + t);
     sh += ldh<H_GLOBAL>(hhi + t);
   }
+#pragma unroll 8
   for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL>(hs + u);
   uint64_t v3[3] = {sl, sh, ss};
   block_excl_scan_n<3>(v3, scratch);
@@ -190,6 +197,7 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
     // cumS_excl(u) = sum_{v < u} H_s(v); start at u = 2 c0 - 1
     const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
     uint64_t cs_excl = baseS - hprev;  // cumS_excl(2 c0 - 1)
+#pragma unroll 8
     for (int t = c0; t < c1; ++t) {
       cl += ldh<H_GLOBAL>(hlo + t);
       ch += ldh<H_GLOBAL>(hhi + t);
@@ -212,6 +220,7 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
     uint64_t cl = baseL, ch = baseH, rlh = baseA, rs = baseG;
     const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
     uint64_t cs_excl = baseS - hprev;
+#pragma unroll 8
     for (int t = c0; t < c1; ++t) {
       cl += ldh<H_GLOBAL>(hlo + t);
       ch += ldh<H_GLOBAL>(hhi + t);
@@ -256,101 +265,114 @@ __device__ __forceinline__ bool is_max_start(const uint64_t* card, const uint64_
   return (b + 1 >= M) || card[b + 1] == 0 || cmp_ratio(sumc[b + 1], card[b + 1], st, ct) < 0;
 }
 
-// Candidate a ranks before candidate b (b = -1: empty).
-__device__ __forceinline__ bool ranks_before(const uint64_t* card, const uint64_t* sumc, int a, int b) {
-  if (b < 0) return true;
+// Candidate a ranks before candidate b: larger C, or equal C and smaller t.  fa,
+// fb are float(sumc) / float(card) (relative error below 2^-22), so a relative
+// gap over 2^-20 between them decides; closer values (and ties) take the exact
+// 128-bit comparison.
+__device__ __forceinline__ bool ranks_before(const uint64_t* card, const uint64_t* sumc, int a, float fa, int b,
+                                             float fb) {
+  constexpr float kGap = 1.00000095367431640625f;  // 1 + 2^-20
+  if (fa > fb * kGap) return true;
+  if (fb > fa * kGap) return false;
   const int c = cmp_ratio(sumc[a], card[a], sumc[b], card[b]);
   return c > 0 || (c == 0 && a < b);
 }
 
-// A warp's sorted top list of L <= 32 candidates: lane r holds rank r (-1:
-// empty).  Inserts the candidates c of the 32 lanes (-1: none): each is first
-// tested against the list's last entry, and only those that beat it are
-// inserted one by one.  Called by all 32 lanes.
-__device__ __forceinline__ void topk_insert(const uint64_t* card, const uint64_t* sumc, int L, int& mine, int c) {
-  const int lane = threadIdx.x & 31;
-  const int last = __shfl_sync(0xffffffffu, mine, L - 1);
-  unsigned m = __ballot_sync(0xffffffffu, c >= 0 && ranks_before(card, sumc, c, last));
-  while (m) {
-    const int src = __ffs(m) - 1;
-    m &= m - 1;
-    const int tn = __shfl_sync(0xffffffffu, c, src);
-    const unsigned worse = __ballot_sync(0xffffffffu, lane < L && ranks_before(card, sumc, tn, mine));
-    if (!worse) continue;
-    const int pos = __ffs(worse) - 1;
-    const int up = __shfl_up_sync(0xffffffffu, mine, 1);
-    if (lane == pos) mine = tn;
-    else if (lane > pos && lane < L) mine = up;
-  }
-}
-
-// Block version (any M, any max_k).  `cand` is scratch for up to (M + 1) / 2 + 1
-// candidates; sh_int holds kShInts ints.
+// One block.  `cand` is scratch of cand_ints(M) ints: the candidate t's, then
+// their float C; sh_int holds kShInts ints.
 __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, int M, int max_k, int32_t* out_t,
                                   int32_t* out_count, int32_t* out_t0, int32_t* cand, int* sh_int,
                                   uint64_t* scratch) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  float* const cf = reinterpret_cast<float*>(cand + cand_ints(M) / 2);
   if (tid == 0) sh_int[0] = 0;
   __syncthreads();
   // 1. plateau starts that are local maxima (in no particular order)
   for (int t = tid; t < M; t += nt)
-    if (is_max_start(card, sumc, M, t)) cand[atomicAdd(&sh_int[0], 1)] = t;
+    if (is_max_start(card, sumc, M, t)) {
+      const int k = atomicAdd(&sh_int[0], 1);
+      cand[k] = t;
+      cf[k] = (float)sumc[t] / (float)card[t];
+    }
   __syncthreads();
   const int K = sh_int[0];
-  if (K <= 64) {
-    // 2a. few maxima: the rank of a candidate is the number of candidates before
-    //     it, one warp per candidate, one comparison per lane and candidate
-    for (int i = warp; i < K; i += nw) {
-      const int ti = cand[i];
-      int before = 0;
-      for (int j = lane; j < K; j += 32) {
-        const int tj = cand[j];
-        if (tj != ti && ranks_before(card, sumc, tj, ti)) ++before;
+  const int need = max_k > 1 ? max_k : 1;  // ranks that matter: below max_k, and rank 0 (t0)
+  // 2. with many candidates, only those whose float C is near or above the
+  //    need-th largest float C can rank below `need`: x = that value, found by a
+  //    radix select on the float bits (non-negative floats order like their
+  //    bits).  A candidate with float C below x (1 - 2^-19) has at least `need`
+  //    candidates certainly before it (their floats exceed its own by more than
+  //    the 2^-20 gap of ranks_before), so it is skipped.
+  float cut = 0.0f;
+  if (K > 64 && K > need) {
+    unsigned* hist = reinterpret_cast<unsigned*>(sh_int + 40);  // 256 counters
+    uint32_t prefix = 0, pmask = 0;
+    int rem = need;  // rank of x among the candidates that match the prefix, from the top
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int b = tid; b < 256; b += nt) hist[b] = 0u;
+      __syncthreads();
+      for (int i = tid; i < K; i += nt) {
+        const uint32_t u = __float_as_uint(cf[i]);
+        if ((u & pmask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
       }
-      before = __reduce_add_sync(0xffffffffu, before);
-      if (lane == 0) {
-        if (out_t && before < max_k) out_t[before] = ti;
-        if (before == 0 && out_t0) *out_t0 = ti;
+      __syncthreads();
+      if (warp == 0) {
+        // lane l holds digits 255 - 8 l .. 248 - 8 l (descending); `above` = count
+        // of larger digits
+        uint32_t c[8], tot = 0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          c[j] = hist[255 - 8 * lane - j];
+          tot += c[j];
+        }
+        uint32_t above = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, above, o);
+          if (lane >= o) above += y;
+        }
+        above -= tot;  // exclusive
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (above < (uint32_t)rem && (uint32_t)rem <= above + c[j]) {
+            sh_int[1] = 255 - 8 * lane - j;
+            sh_int[2] = rem - (int)above;
+          }
+          above += c[j];
+        }
       }
+      __syncthreads();
+      prefix |= (uint32_t)sh_int[1] << shift;
+      pmask |= 255u << shift;
+      rem = sh_int[2];
+      __syncthreads();
     }
-    if (out_t)
-      for (int r = K + tid; r < max_k; r += nt) out_t[r] = -1;
-    if (tid == 0) {
-      if (out_count) *out_count = K;
-      if (K == 0 && out_t0) *out_t0 = -1;
-    }
-    __syncthreads();
-    return;
+    cut = __uint_as_float(prefix) * 0.999996185302734375f;  // x (1 - 2^-18), below x (1 - 2^-19)
   }
-  // 2b. per-warp sorted top lists of the first L candidates in rank order, merged
-  //     by warp 0; with max_k > 32 the list only serves t0 (rank 0)
-  const int L = (max_k > 0 && max_k <= 32) ? max_k : 1;
-  int mine = -1;
-  for (int base = warp * 32; base < K; base += nt) topk_insert(card, sumc, L, mine, base + lane < K ? cand[base + lane] : -1);
-  int* lists = sh_int + 40;  // [nw][32] within the block's kShInts
-  lists[warp * 32 + lane] = mine;
-  __syncthreads();
-  if (warp == 0) {
-    for (int w = 1; w < nw; ++w) topk_insert(card, sumc, L, mine, lists[w * 32 + lane]);
-    if (out_t && max_k <= 32 && lane < max_k) out_t[lane] = mine;  // -1 where fewer than max_k maxima exist
+  // 3. rank of a remaining candidate = number of candidates before it: one warp
+  //    per candidate, one comparison per lane and batch of 32; counting stops
+  //    once the rank reaches `need`
+  for (int i = warp; i < K; i += nw) {
+    const float fi = cf[i];
+    if (fi < cut) continue;
+    const int ti = cand[i];
+    int before = 0;
+    for (int base = 0; base < K && before < need; base += 32) {
+      const int j = base + lane;
+      const bool b = j < K && j != i && ranks_before(card, sumc, cand[j], cf[j], ti, fi);
+      before += __popc(__ballot_sync(0xffffffffu, b));
+    }
     if (lane == 0) {
-      if (out_t0) *out_t0 = mine;
-      if (out_count) *out_count = K;
+      if (out_t && before < max_k) out_t[before] = ti;
+      if (before == 0 && out_t0) *out_t0 = ti;
     }
   }
-  // 3. max_k > 32: rank of each candidate = number of candidates before it
-  if (out_t && max_k > 32) {
-    for (int i = tid; i < K; i += nt) {
-      const int ti = cand[i];
-      int rank = 0;
-      for (int j = 0; j < K && rank < max_k; ++j) {
-        const int tj = cand[j];
-        if (tj != ti && ranks_before(card, sumc, tj, ti)) ++rank;
-      }
-      if (rank < max_k) out_t[rank] = ti;
-    }
+  if (out_t)
     for (int r = K + tid; r < max_k; r += nt) out_t[r] = -1;
+  if (tid == 0) {
+    if (out_count) *out_count = K;
+    if (K == 0 && out_t0) *out_t0 = -1;
   }
   __syncthreads();
 }
@@ -371,7 +393,7 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   uint64_t* card = P.card + (size_t)d.out * M;
   uint64_t* sumc = P.sumc + (size_t)d.out * M;
   double* curve = P.curve ? P.curve + (size_t)d.out * M : nullptr;
-  const size_t need_cs = (size_t)2 * M * 8, need_cand = ((size_t)(M + 1) / 2 + 2) * 4;
+  const size_t need_cs = (size_t)2 * M * 8, need_cand = (size_t)cand_ints(M) * 4;
   const size_t need_h = (size_t)4 * bins * 8;
   const bool stage_cs = dsm_bytes >= need_cs + need_cand;
   const bool stage_h = dsm_bytes >= need_cs + need_cand + need_h;
