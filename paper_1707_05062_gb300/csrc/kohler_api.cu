@@ -26,7 +26,7 @@ struct Workspace {
   int device = -1;
   cudaStream_t stream = nullptr;
   void* mem = nullptr;
-  int slots = 0, bins = 0, cand_stride = 0;
+  int slots = 0, hist_words = 0, cand_stride = 0;
   unsigned long long* hist = nullptr;
   unsigned int* done = nullptr;
   unsigned int* err = nullptr;
@@ -45,10 +45,43 @@ int status_of(cudaError_t e) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Workspace of (current device, stream) with at least `slots` slots of `bins` bins.
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiled encode_tiled() {
+  static EncodeTiled fn = []() -> EncodeTiled {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiled>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of a uint8 image for the strip pass: rows of W / 2 uint16 elements
+// (pixel pairs), `pitch` bytes apart; boxes of 136 elements (a 256-column strip
+// and its 16-byte right halo) by 4 rows; reads outside the image give zeros.
+int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int64_t pitch) {
+  EncodeTiled enc = encode_tiled();
+  if (!enc) return KOHLER_ERR_CUDA;
+  const cuuint64_t dims[2] = {(cuuint64_t)(W / 2), (cuuint64_t)H};
+  const cuuint64_t strides[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {u8h::kBoxW, (cuuint32_t)u8h::kGroupRows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? KOHLER_OK : KOHLER_ERR_CUDA;
+}
+
+// Workspace of (current device, stream) with at least `slots` slots of
+// `hist_words` uint64 histogram words.
 // Newly allocated memory is zeroed on the stream; a replaced workspace is freed
 // after the stream has drained.
-int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Workspace** out) {
+int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_stride, Workspace** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return status_of(e);
@@ -60,12 +93,12 @@ int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Wor
     w->device = dev;
     w->stream = stream;
   }
-  if (w->mem && w->slots >= slots && w->bins >= bins && w->cand_stride >= cand_stride) {
+  if (w->mem && w->slots >= slots && w->hist_words >= hist_words && w->cand_stride >= cand_stride) {
     *out = w;
     return KOHLER_OK;
   }
   slots = std::max(slots, w->slots);
-  bins = std::max(bins, w->bins);
+  hist_words = std::max(hist_words, w->hist_words);
   cand_stride = std::max(cand_stride, w->cand_stride);
   if (w->mem) {
     e = cudaStreamSynchronize(stream);
@@ -73,7 +106,7 @@ int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Wor
     cudaFree(w->mem);
     w->mem = nullptr;
   }
-  const size_t hist_b = align256((size_t)slots * 4 * bins * sizeof(unsigned long long));
+  const size_t hist_b = align256((size_t)slots * hist_words * sizeof(unsigned long long));
   const size_t done_b = align256((size_t)slots * sizeof(unsigned));
   const size_t err_b = align256((size_t)slots * sizeof(unsigned));
   const size_t sticky_b = 256;
@@ -82,7 +115,7 @@ int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Wor
   void* mem = nullptr;
   e = cudaMalloc(&mem, total);
   if (e != cudaSuccess) {
-    w->slots = w->bins = w->cand_stride = 0;
+    w->slots = w->hist_words = w->cand_stride = 0;
     return status_of(e);
   }
   e = cudaMemsetAsync(mem, 0, hist_b + done_b + err_b + sticky_b, stream);
@@ -98,15 +131,17 @@ int get_workspace(cudaStream_t stream, int slots, int bins, int cand_stride, Wor
   w->sticky = reinterpret_cast<unsigned*>(p + hist_b + done_b + err_b);
   w->cand = reinterpret_cast<int32_t*>(p + hist_b + done_b + err_b + sticky_b);
   w->slots = slots;
-  w->bins = bins;
+  w->hist_words = hist_words;
   w->cand_stride = cand_stride;
   *out = w;
   return KOHLER_OK;
 }
 
-enum class Pass { FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16 };
+enum class Pass { HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16 };
 
 int bins_for(kohler_dtype dt, int M) { return dt == KOHLER_U8 ? 256 : ((M + 31) / 32) * 32; }
+// Histogram words per workspace slot: uint8 images keep kHistReplicas copies.
+int hist_words_for(kohler_dtype dt, int M) { return (dt == KOHLER_U8 ? kHistReplicas : 1) * 4 * bins_for(dt, M); }
 
 int check_image(const void* img, kohler_dtype dt, int64_t W, int64_t H, int64_t pitch) {
   if (!img || W < 1 || H < 1) return KOHLER_ERR_ARG;
@@ -128,7 +163,9 @@ int check_common(kohler_dtype dt, int32_t M, kohler_nbhd nb) {
 
 Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
   const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
+  const bool aligned16 = (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0);
   if (dt == KOHLER_U8) {
+    if (aligned16 && im.width % 16 == 0) return M == 256 ? Pass::HistU8 : Pass::HistU8Check;
     if (aligned8 && im.width % 8 == 0) return M == 256 ? Pass::FastU8 : Pass::FastU8Check;
     return Pass::GenericU8;
   }
@@ -139,6 +176,8 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
 
 int strip_px(Pass p) {
   switch (p) {
+    case Pass::HistU8:
+    case Pass::HistU8Check: return u8h::kStripPx;
     case Pass::FastU8:
     case Pass::FastU8Check: return u8r::kStripPx;
     case Pass::FastU16: return 32 * TraitsU16::PX;
@@ -154,6 +193,8 @@ struct KernelInfo {
 
 KernelInfo kernel_for(Pass p, int bins) {
   switch (p) {
+    case Pass::HistU8: return {(const void*)k_u8h<false>, u8h::kNW * 32, (size_t)u8h::kDynBytes};
+    case Pass::HistU8Check: return {(const void*)k_u8h<true>, u8h::kNW * 32, (size_t)u8h::kDynBytes};
     case Pass::FastU8: return {(const void*)k_u8r<false>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16:
@@ -229,7 +270,9 @@ struct Band {
 
 // Rows per work unit: the uint8 pass works on units of 8 rows of a strip, the
 // others on rows.
-bool is_fast_u8(Pass p) { return p == Pass::FastU8 || p == Pass::FastU8Check; }
+bool is_fast_u8(Pass p) {
+  return p == Pass::HistU8 || p == Pass::HistU8Check || p == Pass::FastU8 || p == Pass::FastU8Check;
+}
 int unit_rows(Pass p) { return is_fast_u8(p) ? u8r::kUnitRows : 1; }
 
 // What an image's completion counter counts to: the uint8 pass reports
@@ -272,6 +315,9 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   if (P.n == 0) return KOHLER_OK;
   P.total_rs = rs;
   P.bins = bins;
+  // the strip pass spreads its blocks' merges over the slot's copies; the
+  // others use the first copy
+  P.hist_replicas = (pass == Pass::HistU8 || pass == Pass::HistU8Check) ? kHistReplicas : 1;
   P.M = M;
   KernelInfo k = kernel_for(pass, bins);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
@@ -289,8 +335,20 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  void* args[] = {&P};
-  cudaError_t e = cudaLaunchKernelExC(&cfg, k.fn, args);
+  cudaError_t e;
+  if (pass == Pass::HistU8 || pass == Pass::HistU8Check) {
+    static thread_local ImgMaps T;  // 16 KB: kept off the stack
+    for (int j = 0; j < P.n; ++j) {
+      const ImgDesc& d = P.img[j];
+      const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch);
+      if (rc) return rc;
+    }
+    void* args[] = {&P, &T};
+    e = cudaLaunchKernelExC(&cfg, k.fn, args);
+  } else {
+    void* args[] = {&P};
+    e = cudaLaunchKernelExC(&cfg, k.fn, args);
+  }
   return status_of(e);
 }
 
@@ -305,7 +363,8 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
   const int chunk = std::min<int>(kMaxBatch, std::max<int>(1, (int)std::min<int64_t>(
                                                                kMaxBatch, ((int64_t)256 << 20) / ((int64_t)bins * 32))));
   Workspace* ws = nullptr;
-  int rc = get_workspace(stream, chunk, bins, cand_stride, &ws);
+  const int hist_words = hist_words_for(dt, M);
+  int rc = get_workspace(stream, chunk, hist_words, cand_stride, &ws);
   if (rc) return rc;
   for (int c0 = 0; c0 < n; c0 += chunk) {
     const int cn = std::min(chunk, n - c0);
@@ -323,6 +382,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
     base.out_t0 = out_t0 ? out_t0 + o0 : nullptr;
     base.out_status = out_status ? out_status + o0 : nullptr;
     base.hist = ws->hist;
+    base.hist_stride = hist_words;
     base.done = ws->done;
     base.err = ws->err;
     base.sticky = ws->sticky;
@@ -406,7 +466,7 @@ int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   const int cand_stride = cand_ints(M);
   Workspace* ws = nullptr;
-  int rc = get_workspace(stream, kMaxBatch, 32, cand_stride, &ws);
+  int rc = get_workspace(stream, kMaxBatch, 128, cand_stride, &ws);
   if (rc) return rc;
   for (int c0 = 0; c0 < n; c0 += kMaxBatch) {
     const int cn = std::min(kMaxBatch, n - c0);
@@ -675,6 +735,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr size_t kCountersAt = (size_t)4 * kNoAllocMaxM * 8;      // 131072
 constexpr size_t kCandAt = kCountersAt + 256;
 static_assert(kCandAt + (size_t)cand_ints(kNoAllocMaxM) * 4 <= kNoAllocScratchBytes, "scratch too small");
+static_assert((size_t)kHistReplicas * 4 * 256 * 8 <= kCountersAt, "uint8 histogram copies must fit below the counters");
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal (set up once)
@@ -733,6 +794,7 @@ extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t 
   base.out_t0 = out_t0;
   base.out_status = out_status;
   base.hist = reinterpret_cast<unsigned long long*>(s);
+  base.hist_stride = hist_words_for(dt, M);  // one slot: fits below kCountersAt
   base.done = reinterpret_cast<unsigned*>(s + kCountersAt);
   base.err = reinterpret_cast<unsigned*>(s + kCountersAt + 4);
   base.sticky = reinterpret_cast<unsigned*>(s + kCountersAt + 8);

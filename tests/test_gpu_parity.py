@@ -122,6 +122,33 @@ def test_u8_small_M(M):
     assert_same(run_analyze([to_dev(img2)], M)[0], expect(img2, M))
 
 
+# Images whose base, pitch and width are multiples of 16 bytes take the uint8
+# route that streams 256-column strips through bulk copies: widths that leave
+# a ragged last strip (16 .. 240 columns), one-row and two-row images, pitches
+# wider than the row, and M < 256 (range checked on the device).
+U8H_SHAPES = [(1, 16), (2, 16), (1, 32), (3, 272), (5, 512), (50, 528), (129, 784), (33, 4112), (300, 5184), (2, 1296)]
+
+
+@pytest.mark.parametrize("h,w", U8H_SHAPES)
+@pytest.mark.parametrize("kind", ["smooth", "random"])
+def test_u8_strip_route_shapes(h, w, kind):
+    seed = 7 * h + w
+    img = synth.smooth_image(seed, w, h, 256) if kind == "smooth" else synth.random_image(seed, w, h, 256)
+    assert_same(run_analyze([to_dev(img)], 256)[0], expect(img, 256), f"{h}x{w}")
+
+
+@pytest.mark.parametrize("M,pad", [(2, 16), (61, 0), (200, 48)])
+def test_u8_strip_route_small_M_and_pitch(M, pad):
+    img = synth.smooth_image(M + pad, 800, 45, M)
+    assert_same(run_analyze([to_dev(img, pad)], M)[0], expect(img, M), f"M={M} pad={pad}")
+
+
+def test_u8_strip_route_many_rounds():
+    # 160 000 strip-rows: every block folds its lane copies more than once
+    img = synth.smooth_image(5, 1024, 40000, 256)
+    assert_same(run_analyze([to_dev(img)], 256)[0], expect(img, 256), "1024x40000")
+
+
 @pytest.mark.parametrize("M,h,w", [(4096, 33, 132), (4096, 20, 131), (1000, 40, 64), (300, 17, 30), (65536, 9, 37),
                                    (8192, 12, 40)])
 def test_u16(M, h, w):
@@ -304,7 +331,7 @@ def test_two_streams_concurrently():
 
 
 # ------------------------------------------------------------------------ host-buffer path
-@pytest.mark.parametrize("shape", [(1, 1), (37, 100), (600, 1032)])
+@pytest.mark.parametrize("shape", [(1, 1), (37, 100), (600, 1032), (600, 1024)])
 def test_analyze_host(shape):
     k = K()
     img = synth.smooth_image(shape[0] + shape[1], shape[1], shape[0], 256)
