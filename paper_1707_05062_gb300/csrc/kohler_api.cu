@@ -140,8 +140,8 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
 enum class Pass { HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16 };
 
 int bins_for(kohler_dtype dt, int M) { return dt == KOHLER_U8 ? 256 : ((M + 31) / 32) * 32; }
-// Histogram words per workspace slot: uint8 images keep kHistReplicas copies.
-int hist_words_for(kohler_dtype dt, int M) { return (dt == KOHLER_U8 ? kHistReplicas : 1) * 4 * bins_for(dt, M); }
+// Histogram words per workspace slot.
+int hist_words_for(kohler_dtype dt, int M) { return 4 * bins_for(dt, M); }
 
 int check_image(const void* img, kohler_dtype dt, int64_t W, int64_t H, int64_t pitch) {
   if (!img || W < 1 || H < 1) return KOHLER_ERR_ARG;
@@ -315,9 +315,6 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   if (P.n == 0) return KOHLER_OK;
   P.total_rs = rs;
   P.bins = bins;
-  // the strip pass spreads its blocks' merges over the slot's copies; the
-  // others use the first copy
-  P.hist_replicas = (pass == Pass::HistU8 || pass == Pass::HistU8Check) ? kHistReplicas : 1;
   P.M = M;
   KernelInfo k = kernel_for(pass, bins);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
@@ -735,7 +732,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr size_t kCountersAt = (size_t)4 * kNoAllocMaxM * 8;      // 131072
 constexpr size_t kCandAt = kCountersAt + 256;
 static_assert(kCandAt + (size_t)cand_ints(kNoAllocMaxM) * 4 <= kNoAllocScratchBytes, "scratch too small");
-static_assert((size_t)kHistReplicas * 4 * 256 * 8 <= kCountersAt, "uint8 histogram copies must fit below the counters");
 
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {};  // device address of the array, per device ordinal (set up once)

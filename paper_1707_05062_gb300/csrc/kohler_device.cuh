@@ -37,7 +37,6 @@ constexpr int kMaxBatch = 128;      // images per launch (descriptors travel in 
 constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
 constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, warp winners, per-warp top lists
 constexpr int kScratch = 3 * 33;       // shared uint64 scratch of a block (block scans of up to 3 values)
-constexpr int kHistReplicas = 8;       // global histogram copies per uint8 image (block b merges into copy b % 8)
 
 // Ints of threshold-candidate scratch for M levels: up to (M + 1) / 2 + 1
 // candidates, each with its t and the float of its C.
@@ -72,9 +71,8 @@ struct LaunchParams {
   int32_t* out_t0;            // [out] or null
   int32_t* out_status;        // [out] or null: KOHLER_OK or KOHLER_ERR_RANGE per image
   // workspace (device)
-  unsigned long long* hist;   // [slot][hist_stride]: replicas of H_lo[bins], H_hi[bins], H_s[2 * bins]
-  int64_t hist_stride;        // uint64 per slot (>= hist_replicas * 4 * bins)
-  int32_t hist_replicas;      // copies of the histograms per slot that blocks spread their merges over
+  unsigned long long* hist;   // [slot][hist_stride]: H_lo[bins], H_hi[bins], H_s[2 * bins]
+  int64_t hist_stride;        // uint64 per slot (>= 4 * bins)
   unsigned int* done;         // [slot] row-strips reduced so far
   unsigned int* err;          // [slot] error bits of the image
   unsigned int* sticky;       // error bits of the stream (read by kohler_stream_status)
@@ -400,19 +398,6 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   const int M = P.M, bins = P.bins;
   unsigned long long* h = P.hist + (size_t)d.slot * P.hist_stride;
   __threadfence();
-  if (P.hist_replicas > 1) {  // add the other copies into the first and clear them
-    for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) {
-      unsigned long long v = __ldcg(h + b);
-      for (int r = 1; r < P.hist_replicas; ++r) {
-        unsigned long long* q = h + (size_t)r * 4 * bins + b;
-        v += __ldcg(q);
-        *q = 0ull;
-      }
-      h[b] = v;
-    }
-    __threadfence_block();
-    __syncthreads();
-  }
   const bool bad = (__ldcg(P.err + d.slot) & kErrRange) != 0;
   uint64_t* card = P.card + (size_t)d.out * M;
   uint64_t* sumc = P.sumc + (size_t)d.out * M;
@@ -1135,14 +1120,12 @@ __device__ __forceinline__ void red_s_hi(uint32_t addr, uint32_t v) {  // the bi
 }
 
 // Folds the lane copies of the region into image i's global histograms and
-// clears the region.  512 threads: thread t owns region row t; it reads the row
+// (if `clear`) clears the region.  512 threads: thread t owns region row t; it reads the row
 // in 16-byte chunks rotated by t, so that the 8 threads of a quarter warp hit
 // distinct banks.
-__device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uint32_t* region, uint32_t* xch) {
-  // this block's copy of the image's histograms: blocks spread over the copies
-  // so that fewer of them add into the same global words at once
-  unsigned long long* g =
-      P.hist + (size_t)P.img[i].slot * P.hist_stride + (size_t)(blockIdx.x % P.hist_replicas) * (4 * 256);
+__device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uint32_t* region, uint32_t* xch,
+                                               bool clear) {
+  unsigned long long* g = P.hist + (size_t)P.img[i].slot * P.hist_stride;
   const int t = threadIdx.x;
   uint4* const row = reinterpret_cast<uint4*>(region + 64 * t);
   uint32_t hs = 0, tm = 0, se = 0;
@@ -1151,7 +1134,7 @@ __device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uin
   for (int c = 0; c < 8; ++c) {
     const int cc = (c + t) & 7;
     const uint4 w = row[cc];
-    row[cc] = make_uint4(0u, 0u, 0u, 0u);
+    if (clear) row[cc] = make_uint4(0u, 0u, 0u, 0u);
     hs += w.x + w.y + w.z + w.w;
   }
   if (t < 256) {
@@ -1159,7 +1142,7 @@ __device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uin
     for (int c = 0; c < 8; ++c) {
       const int cc = 8 + ((c + t) & 7);
       const uint4 w = row[cc];
-      row[cc] = make_uint4(0u, 0u, 0u, 0u);
+      if (clear) row[cc] = make_uint4(0u, 0u, 0u, 0u);
       const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -1173,7 +1156,7 @@ __device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uin
     for (int c = 0; c < 8; ++c) {
       const int cc = 8 + ((c + t) & 7);
       const uint4 w = row[cc];
-      row[cc] = make_uint4(0u, 0u, 0u, 0u);
+      if (clear) row[cc] = make_uint4(0u, 0u, 0u, 0u);
       tm += w.x + w.y + w.z + w.w;
     }
     xch[t - 256] = tm;
@@ -1243,18 +1226,19 @@ __device__ __forceinline__ void u8h_load(uint32_t ra, uint32_t K, bool lastc, ui
 
 // One whole ring group: rows y .. y + 3 (Pc holds row y on entry and row y + 4
 // on exit) with the group's four rows as their lower rows.  All eight loads are
-// issued before the first row is reduced.
+// issued before the first row is reduced.  Row y takes the vertical-word
+// constant Dt (it differs from Dm only for the image's first row).
 template <bool CHECK, bool FULL>
 __device__ __forceinline__ void u8h_group(uint32_t ra, uint32_t K, bool act, bool lastc, uint32_t (&Pc)[9],
-                                          uint32_t (&Pn)[9], uint32_t (&mU)[8], uint32_t D0, uint32_t Dm, uint32_t D7,
-                                          uint32_t C, uint32_t& vmax) {
+                                          uint32_t (&Pn)[9], uint32_t (&mU)[8], uint32_t Dt, uint32_t D0, uint32_t Dm,
+                                          uint32_t D7, uint32_t C, uint32_t& vmax) {
   using u8h::kRowBytes;
   const uint2 w0 = lds64(ra), w1 = lds64(ra + kRowBytes), w2 = lds64(ra + 2 * kRowBytes), w3 = lds64(ra + 3 * kRowBytes);
   const uint32_t r0 = lds32(ra + 8u), r1 = lds32(ra + kRowBytes + 8u), r2 = lds32(ra + 2 * kRowBytes + 8u),
                  r3 = lds32(ra + 3 * kRowBytes + 8u);
   const bool lc = FULL ? false : lastc;
   u8h_bins(w0, r0, K, lc, Pn);
-  if (FULL || act) u8h_row<CHECK>(Pc, Pn, mU, D0, Dm, D7, C, vmax);
+  if (FULL || act) u8h_row<CHECK>(Pc, Pn, mU, D0 + (Dt - Dm), Dt, D7 + (Dt - Dm), C, vmax);  // Dt: first row's constant
   u8h_bins(w1, r1, K, lc, Pc);
   if (FULL || act) u8h_row<CHECK>(Pn, Pc, mU, D0, Dm, D7, C, vmax);
   u8h_bins(w2, r2, K, lc, Pn);
@@ -1293,11 +1277,11 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   rg.failed = false;
   if (lane == 0)
     for (int s = 0; s < kSlots; ++s) mbar_init(rg.bar0 + 8u * s, 1u);
+  if (threadIdx.x == 0) sh_rows = 0u;
   {
     uint4* r4 = reinterpret_cast<uint4*>(region);
     for (int k = threadIdx.x; k < (int)(kRegionBytes / 16); k += blockDim.x) r4[k] = make_uint4(0u, 0u, 0u, 0u);
   }
-  if (threadIdx.x == 0) sh_rows = 0u;
   fence_mbar_init();
   __syncthreads();
   allow_dependents();
@@ -1326,10 +1310,12 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
       const uint32_t b = (uint32_t)(base - d.rs_begin) + (uint32_t)((n_r * (warp + 1)) / kNW);
       uint32_t rows_done = 0;
       // Producer: walks the same runs as the reduction below and keeps the ring
-      // full, across run boundaries.  Group g of a run holds rows yfirst + 4 g ..
-      // + 3 of its strip (columns x0 .. x0 + 271).
+      // full, across run boundaries.  Group g of a run [ya, yb[ holds rows
+      // ya - 3 + 4 g .. ya + 4 g of its strip (columns x0 .. x0 + 271): group 0
+      // ends with the run's first row, so the rows the run reduces start on a
+      // group boundary.  Rows above the image read as zeros and are skipped.
       uint32_t pa = a;                 // first unit of the next run to produce
-      int p_x0 = 0, p_yfirst = 0, p_ngroups = 0, p_gi = 0;
+      int p_x0 = 0, p_y0 = 0, p_ngroups = 0, p_gi = 0;
       auto produce = [&]() {
         while (p_gi == p_ngroups) {
           if (pa >= b) return;
@@ -1339,8 +1325,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
           pa += (uint32_t)(ub - ua);
           const int ya = d.y0 + ua, yb = d.y0 + ub;
           p_x0 = strip * kStripPx;
-          p_yfirst = ya > 0 ? ya - 1 : ya;
-          p_ngroups = (min(yb, H - 1) - p_yfirst + kGroupRows) / kGroupRows;
+          p_y0 = ya - 3;
+          p_ngroups = (min(yb, H - 1) - p_y0 + kGroupRows) / kGroupRows;
           p_gi = 0;
         }
         const uint32_t slot = rg.islot;
@@ -1349,7 +1335,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
           const uint32_t bar = rg.bar0 + 8u * slot;
           fence_proxy_async();
           mbar_expect_tx(bar, kBoxBytes);
-          tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_yfirst + p_gi * kGroupRows, bar);
+          tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_y0 + p_gi * kGroupRows, bar);
         }
         ++p_gi;
       };
@@ -1374,10 +1360,9 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         const bool lastc = act && (xl + 8 == W);
         const uint32_t xadj0 = (xl == 0) ? 0x10000u : 0u;  // no left neighbour: one end fewer
         const uint32_t xadj7 = lastc ? 0x10000u : 0u;       // padding right pair: one end more
-        const int yfirst = ya > 0 ? ya - 1 : ya;
         const int ylim = min(yb, H - 1);              // the last row read
-        const int nrows = ylim - yfirst + 1;          // rows yfirst .. ylim
-        int jr = 0;  // rows of this run read
+        const int nrows = ylim - (ya - 3) + 1;        // ring rows of the run: ya - 3 .. ylim
+        int jr = 0;  // ring rows of this run read or skipped
         auto read_row = [&](uint32_t(&Q)[9]) {
           if (rg.rin == 0) wait_group();
           u8h_load(rg.cur + (uint32_t)rg.rin * kRowBytes, K, lastc, Q);
@@ -1389,6 +1374,9 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
           }
         };
         uint32_t Pc[9], Pn[9], mU[8];
+        wait_group();  // group 0: rows ya - 3 .. ya; the first 2 (3 at the image top) are not needed
+        rg.rin = ya > 0 ? 2 : 3;
+        jr = rg.rin;
         if (ya > 0) {
           read_row(Pn);  // the row above
           read_row(Pc);
@@ -1415,17 +1403,17 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
 #pragma unroll
           for (int k = 0; k < 9; ++k) Pc[k] = Pn[k];
         };
-        // Pc holds row y = yfirst + jr - 1; rows are reduced in order
+        // Pc holds row y; rows are reduced in order.  Whole groups of rows first:
+        // rows y .. y + 3 with lower rows y + 1 .. y + 4 (the group's four rows);
+        // the row buffers swap roles, no copies
         int y = ya;
-        if (y == 0 && y < yb) row_any(y++);
-        while (y < yb && (rg.rin != 0 || y + kGroupRows > ylim)) row_any(y++);  // up to a group boundary
-        // whole groups of interior rows: rows y .. y + 3 with lower rows y + 1 .. y + 4
-        // (the group's four rows); the row buffers swap roles, no copies
-        const uint32_t Dm = (4u << 16) - 1u;
+        const uint32_t Dm = (4u << 16) - 1u;            // interior rows: 4 pair ends, low field -1 + mD - mU
+        const uint32_t Dtop = (3u << 16) - 1u;          // the image's first row: no upper neighbour
         if (full) {
           while (y + kGroupRows <= ylim) {
             wait_group();
-            u8h_group<CHECK, true>(rg.cur, K, act, lastc, Pc, Pn, mU, Dm - xadj0, Dm, Dm, C, vmax);
+            const uint32_t Dt = y == 0 ? Dtop : Dm;
+            u8h_group<CHECK, true>(rg.cur, K, act, lastc, Pc, Pn, mU, Dt, Dm - xadj0, Dm, Dm, C, vmax);
             y += kGroupRows;
             jr += kGroupRows;
             __syncwarp();
@@ -1434,7 +1422,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         } else {
           while (y + kGroupRows <= ylim) {
             wait_group();
-            u8h_group<CHECK, false>(rg.cur, K, act, lastc, Pc, Pn, mU, Dm - xadj0, Dm, Dm + xadj7, C, vmax);
+            const uint32_t Dt = y == 0 ? Dtop : Dm;
+            u8h_group<CHECK, false>(rg.cur, K, act, lastc, Pc, Pn, mU, Dt, Dm - xadj0, Dm, Dm + xadj7, C, vmax);
             y += kGroupRows;
             jr += kGroupRows;
             __syncwarp();
@@ -1446,7 +1435,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
       if (lane == 0 && rows_done) atomicAdd(&sh_rows, rows_done);
       wait_prior();
       __syncthreads();
-      u8h_fold_flush(P, i, region, xch);
+      u8h_fold_flush(P, i, region, xch, base + (int64_t)kNW * kRowsPerRound < seg_end);
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
