@@ -326,7 +326,7 @@ def bench_ours(args, rank, local, world, dist):
     mean_launch_s = dev_s / args.steps  # one launch per step, back to back
     peak, peak_src = measured_peak_hbm()
     achieved = px / mean_launch_s / 1e9  # algorithmic bytes: one read of each 1-byte pixel
-    traffic = kernel_traffic("k_u8r", "voronoi_18mp")
+    traffic = kernel_traffic("k_u8h", "voronoi_18mp")
     e2e = bench_e2e(args, pool_np, M, rank, dist) if not args.no_e2e else None
     cpu = cpu_baseline(pool_np[0], M) if (rank == 0 and world == 1 and not args.no_cpu) else None
     del pool
@@ -342,7 +342,7 @@ def bench_ours(args, rank, local, world, dist):
                    "launch": "CUDA-graph replays, 48 fused launches per graph"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"hbm_gbs of {peak_src}",
-                     "kernel": "k_u8r (fused pass + epilogue + thresholds)",
+                     "kernel": "k_u8h (fused pass + epilogue + thresholds)",
                      "mean_launch_us": mean_launch_s * 1e6,
                      "isolated_launch_p50_us": float(np.median(launch_ms)) * 1e3,
                      "host_launched_us_per_step": host_launched_us},
