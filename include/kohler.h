@@ -106,11 +106,10 @@ int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, i
                          int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
                          int32_t* out_count, int32_t* out_t0, void* cuda_stream);
 
-/* Whole path from HOST memory and back, synchronously.  A pinned (page-locked,
- * device-mapped) image is read by the kernel itself over the host link, with no
- * staging copy; any other image is copied to the device in row bands on a copy
- * stream while earlier bands are already being reduced.  Then card/sumc/curve
- * and the thresholds are copied back.
+/* Whole path from HOST memory and back, synchronously.  The image is copied to
+ * the device in row bands on a copy stream while earlier bands are already
+ * being reduced (from pinned memory the copies are asynchronous and fastest).
+ * Then card/sumc/curve and the thresholds are copied back.
  * img: host pointer; outputs: HOST arrays card/sumc uint64[M], curve double[M],
  * out_t int32[max_k] (any output may be NULL).  Returns KOHLER_ERR_RANGE directly
  * for a pixel >= M. */

@@ -191,10 +191,15 @@ struct KernelInfo {
   size_t smem;
 };
 
-KernelInfo kernel_for(Pass p, int bins) {
+// `single`: the launch holds one image (the strip pass then takes one tensor map).
+KernelInfo kernel_for(Pass p, int bins, bool single) {
   switch (p) {
-    case Pass::HistU8: return {(const void*)k_u8h<false>, u8h::kNW * 32, (size_t)u8h::kDynBytes};
-    case Pass::HistU8Check: return {(const void*)k_u8h<true>, u8h::kNW * 32, (size_t)u8h::kDynBytes};
+    case Pass::HistU8:
+      return {single ? (const void*)k_u8h<false, 1> : (const void*)k_u8h<false, kMaxBatch>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
+    case Pass::HistU8Check:
+      return {single ? (const void*)k_u8h<true, 1> : (const void*)k_u8h<true, kMaxBatch>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
     case Pass::FastU8: return {(const void*)k_u8r<false>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16:
@@ -316,7 +321,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   P.total_rs = rs;
   P.bins = bins;
   P.M = M;
-  KernelInfo k = kernel_for(pass, bins);
+  KernelInfo k = kernel_for(pass, bins, P.n == 1);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
   P.smem_bytes = (int32_t)k.smem;
   int grid = grid_for(k, rs, is_fast_u8(pass) ? 2 : kRowsPerWarp);
@@ -333,8 +338,15 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if (pass == Pass::HistU8 || pass == Pass::HistU8Check) {
-    static thread_local ImgMaps T;  // 16 KB: kept off the stack
+  if ((pass == Pass::HistU8 || pass == Pass::HistU8Check) && P.n == 1) {
+    // one image: the kernel instance that takes a single tensor map
+    ImgMaps<1> T1;
+    const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch);
+    if (rc) return rc;
+    void* args[] = {&P, &T1};
+    e = cudaLaunchKernelExC(&cfg, k.fn, args);
+  } else if (pass == Pass::HistU8 || pass == Pass::HistU8Check) {
+    static thread_local ImgMaps<kMaxBatch> T;  // 16 KB: kept off the stack
     for (int j = 0; j < P.n; ++j) {
       const ImgDesc& d = P.img[j];
       const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch);
@@ -634,23 +646,18 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   const size_t o_card = 0, o_sumc = (size_t)M * 8, o_curve = 2 * (size_t)M * 8, o_t = 3 * (size_t)M * 8;
   const size_t o_cnt = o_t + ((size_t)std::max(max_k, 1) * 4 + 15) / 16 * 16, o_t0 = o_cnt + 16;
   const size_t out_bytes = o_t0 + 16;
-  // Pinned (or otherwise device-mapped) host memory is read by the pass itself,
-  // over the host link, with no staging copy; other memory is copied in bands.
-  cudaPointerAttributes pa;
-  const void* mapped = nullptr;
-  if (cudaPointerGetAttributes(&pa, img) == cudaSuccess) {
-    if (pa.type == cudaMemoryTypeHost && pa.devicePointer) mapped = pa.devicePointer;
-  } else {
-    cudaGetLastError();  // an unknown pointer is ordinary pageable memory
-  }
+  // The image is copied to the device in bands by the copy engine (pinned
+  // memory: asynchronously), each band reduced while the next one is copied.
+  // Reading pinned memory from the pass itself, over the host link, is about
+  // half as fast as the copy engine on this path, so it is not used.
   // packed rows are copied as they are (one contiguous copy per band); others go
   // to rows padded to 128 bytes
   const bool packed = pitch_bytes == width * es && (width * es) % 8 == 0;
   const int64_t dpitch = packed ? width * es : ((width * es + 127) / 128) * 128;
-  const size_t img_bytes = mapped ? 0 : (size_t)dpitch * height;
+  const size_t img_bytes = (size_t)dpitch * height;
   // bands of rows: copy band b + 1 while band b is reduced (a band needs the first
   // row of the next band for its lower pairs)
-  const int nbands = mapped ? 1 : (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
+  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
   std::lock_guard<std::mutex> lock(g_host_mu);
   HostPath* h = nullptr;
   rc = host_path(&h, img_bytes, out_bytes, nbands + 1);
@@ -664,10 +671,7 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
                      band);
   };
   cudaError_t e = cudaSuccess;
-  if (mapped) {
-    rc = reduce(kohler_image{mapped, width, height, pitch_bytes}, nullptr);
-    if (rc) return rc;
-  } else {
+  {
     char* dimg = static_cast<char*>(h->dimg);
     // band edges on multiples of 8 rows
     std::vector<int32_t> yb(nbands + 1);

@@ -84,9 +84,11 @@ struct LaunchParams {
 
 // Tensor maps of the images of one launch of the uint8 strip pass (entry i
 // belongs to img[i]): the image's rows viewed as pairs of pixels (uint16
-// elements), so that a 272-byte row segment is one box row.
-struct alignas(64) ImgMaps {
-  CUtensorMap map[kMaxBatch];
+// elements), so that a 272-byte row segment is one box row.  Launches of one
+// image pass a single map (smaller kernel parameters, faster launches).
+template <int N>
+struct ImgMaps {
+  CUtensorMap map[N];  // 128-byte aligned entries
 };
 
 // ----------------------------------------------------------------------------- small helpers
@@ -1247,9 +1249,9 @@ __device__ __forceinline__ void u8h_group(uint32_t ra, uint32_t K, bool act, boo
   if (FULL || act) u8h_row<CHECK>(Pn, Pc, mU, D0, Dm, D7, C, vmax);
 }
 
-template <bool CHECK>
+template <bool CHECK, int NMAP>
 __global__ void __launch_bounds__(u8h::kNW * 32, 1)
-    k_u8h(const __grid_constant__ LaunchParams P, const __grid_constant__ ImgMaps T) {
+    k_u8h(const __grid_constant__ LaunchParams P, const __grid_constant__ ImgMaps<NMAP> T) {
   using namespace u8h;
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ uint64_t scratch[kScratch];
@@ -1299,7 +1301,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   int i = r0 < r1 ? image_of(P, r0) : 0;
   while (r0 < r1) {
     const ImgDesc& d = P.img[i];
-    const CUtensorMap* const map = &T.map[i];
+    const CUtensorMap* const map = &T.map[NMAP == 1 ? 0 : i];
     const int units_col = d.y1 - d.y0;  // rows per strip in this launch
     const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * units_col);
     const int W = d.W, H = d.H;

@@ -344,7 +344,7 @@ def test_analyze_host(shape):
 
 @pytest.mark.parametrize("dtype,w,h,M", [(np.uint8, 1000, 600, 256), (np.uint8, 333, 101, 200), (np.uint16, 516, 130, 4096)])
 def test_analyze_host_pinned(dtype, w, h, M):
-    # pinned host memory is read by the kernel directly (no staging copy)
+    # pinned host memory: the banded copies run asynchronously
     img = synth.smooth_image(91, w, h, M, dtype)
     src = torch.from_numpy(img.view(np.int16) if dtype == np.uint16 else img).pin_memory()
     got = K().analyze_host(src, M, MAX_K)
