@@ -145,3 +145,36 @@ def analyze(img: np.ndarray, M: int, max_k: int, method: str = "alg1"):
     c = normalise(card, sumc)
     ts, cnt, t0 = thresholds(card, sumc, max_k)
     return card, sumc, c, ts, cnt, t0
+
+
+def segment(img: np.ndarray, M: int, thresholds) -> np.ndarray:
+    """Segmentation of an image by a set of thresholds (Section 2.1: the classes
+    C_0^t = {f <= t} and C_1^t = {f > t} of one threshold; Fig. 1 and its
+    caption: several thresholds, each class shown as the mean value of its
+    pixels; Section 4: two-class segmentation of video frames).
+
+    The thresholds in [0, M[ (others dropped), sorted and without repeats,
+    t_1 < ... < t_k, cut the grey levels into k + 1 classes: C_0 = {f <= t_1},
+    C_i = {t_i < f <= t_{i+1}}, C_k = {f > t_k}; the class of a pixel is the
+    number of thresholds strictly below its value.  Every pixel takes the mean
+    value of its class, rounded half up to an integer: floor((2 S + n) / (2 n))
+    for a class of n pixels whose values sum to S.  Returns an array of the
+    image's shape and dtype.  A pixel >= M raises OracleError (range)."""
+    f = np.asarray(img)
+    if f.ndim != 2 or f.dtype not in (np.uint8, np.uint16):
+        raise OracleError("image must be a 2-D uint8/uint16 array")
+    if f.size and int(f.max()) >= M:
+        raise OracleError(f"oracle returned {ERR_RANGE}")
+    ts = sorted({int(t) for t in thresholds if 0 <= int(t) < M})
+    v = f.astype(np.int64)
+    cls = np.zeros(f.shape, np.int64)
+    for t in ts:
+        cls += v > t
+    out = np.zeros_like(f)
+    for c in range(len(ts) + 1):
+        mask = cls == c
+        n = int(mask.sum())
+        if n:
+            s = int(v[mask].sum())
+            out[mask] = (2 * s + n) // (2 * n)
+    return out
