@@ -649,6 +649,49 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
     return out
 
 
+def form_segment(K, torch, dev, peak, n_pool=6):
+    """Segmentation of the 18-Mpixel images by their own ranked thresholds (each
+    pixel replaced by its class mean), the thresholds and their count passed
+    on the device from a preceding analyze call: kohler_segment alone, and the
+    whole analyze + segment per image, both as CUDA-graph replays cycling
+    n_pool images and outputs (more bytes than L2)."""
+    import oracle
+    import synth
+
+    pool_np = synth.voronoi_18mp_pool(n_pool)
+    H, W = pool_np[0].shape
+    px = W * H
+    imgs = [torch.from_numpy(im).to(dev) for im in pool_np]
+    outs = [torch.empty_like(im) for im in imgs]
+    res_an = [K.analyze_batch([im], 256, 6) for im in imgs]
+    torch.cuda.synchronize(dev)
+
+    def seg_only(s):
+        for j in range(n_pool):
+            K.segment(imgs[j], 256, res_an[j][3][0], res_an[j][4][0], out=outs[j], stream=s)
+
+    def whole(s):
+        for j in range(n_pool):
+            K.analyze_batch([imgs[j]], 256, 6, out=res_an[j], stream=s)
+            K.segment(imgs[j], 256, res_an[j][3][0], res_an[j][4][0], out=outs[j], stream=s)
+
+    g1, s1 = _graph_of(torch, dev, seg_only)
+    t_seg = _time_graph(torch, g1, s1, 20) / n_pool
+    g2, s2 = _graph_of(torch, dev, whole)
+    t_all = _time_graph(torch, g2, s2, 20) / n_pool
+    if K.stream_status(s1) != K.OK or K.stream_status(s2) != K.OK:
+        raise RuntimeError("segment: a launch reported an error")
+    ts = res_an[0][3][0].cpu().numpy()
+    want = oracle.segment(pool_np[0], 256, [int(t) for t in ts if t >= 0])
+    moved = 3 * px  # the image read by the level-count pass and by the map pass, the output written
+    return {"workload": f"{W}x{H} uint8 Voronoi images, M = 256, their 6 ranked thresholds (7 classes)",
+            "segment_ms": t_seg * 1e3, "segment_gpx_s": px / t_seg / 1e9,
+            "segment_bytes_per_image": moved, "segment_hbm_frac": moved / t_seg / 1e9 / peak,
+            "analyze_plus_segment_ms": t_all * 1e3, "analyze_plus_segment_gpx_s": px / t_all / 1e9,
+            "parity_spot_check": bool(np.array_equal(outs[0].cpu().numpy(), want)),
+            "launch": f"CUDA-graph replays of {n_pool} images"}
+
+
 def run_forms(args, K, torch, dev, peak):
     forms = {}
     names = [x for x in args.forms.split(",") if x]
@@ -673,6 +716,8 @@ def run_forms(args, K, torch, dev, peak):
                 forms[name]["parity_spot_check"]["note"] = "full-size parity: tests/test_gpu_parity.py (slow mark)"
             elif name == "served":
                 forms[name] = form_served(K, torch, dev)
+            elif name == "segment":
+                forms[name] = form_segment(K, torch, dev, peak)
             else:
                 forms[name] = {"error": "unknown form"}
         except Exception as e:  # a failing form is reported, not hidden
@@ -726,7 +771,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served",
+    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served,segment",
                     help="comma list of extra forms reported in the same line (N = 1 only); empty for none")
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -106,6 +106,26 @@ int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, i
                          int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
                          int32_t* out_count, int32_t* out_t0, void* cuda_stream);
 
+/* Segmentation by thresholds (Section 2.1: a threshold t makes the classes
+ * C_0 = {f <= t} and C_1 = {f > t}; Fig. 1 and its caption: several thresholds
+ * cut the grey levels into classes, each shown as the mean value of its pixels;
+ * Section 4: two-class segmentation of video frames).
+ * The distinct thresholds t_1 < ... < t_k in [0, M[ (others ignored: e.g. the -1
+ * padding of kohler_analyze_batch's out_t) make the k + 1 classes
+ * C_0 = {f <= t_1}, C_i = {t_i < f <= t_{i+1}}, C_k = {f > t_k}; every output
+ * pixel is the mean value of its class rounded half up, floor((2 S + n) / (2 n))
+ * for a class of n pixels summing to S (exact integers).
+ * img: device image (as kohler_curve); thresholds: device int32[max_k], any order;
+ * count: device int32, only the first *count entries are used (NULL: all max_k;
+ * pass kohler_analyze_batch's out_count); out: caller-owned device image of the
+ * same dtype, out_pitch_bytes >= width * element size (uint16: 2-byte aligned).
+ * Asynchronous on cuda_stream (two kernel launches); scratch is cached per
+ * stream.  A pixel >= M makes the output all zero and the next
+ * kohler_stream_status return KOHLER_ERR_RANGE.  Bad arguments: KOHLER_ERR_ARG. */
+int kohler_segment(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes, int32_t M,
+                   const int32_t* thresholds, const int32_t* count, int32_t max_k, void* out,
+                   int64_t out_pitch_bytes, void* cuda_stream);
+
 /* Whole path from HOST memory and back, synchronously.  The image is copied to
  * the device in row bands on a copy stream while earlier bands are already
  * being reduced (from pinned memory the copies are asynchronous and fastest).

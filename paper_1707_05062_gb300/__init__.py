@@ -63,6 +63,7 @@ def lib():
             L.kohler_analyze_batch.argtypes = [p, i32, i, i32, i, i32, p, p, p, p, p, p, p]
             L.kohler_analyze_host.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p]
             L.kohler_stream_status.argtypes = [p]
+            L.kohler_segment.argtypes = [p, i, i64, i64, i64, i32, p, p, i32, p, i64, p]
             if hasattr(L, "kohler_analyze_noalloc"):
                 L.kohler_analyze_noalloc.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p, p, p]
                 L.kohler_analyze_noalloc.restype = i
@@ -70,7 +71,7 @@ def lib():
             L.kohler_strerror.argtypes = [i]
             L.kohler_strerror.restype = ctypes.c_char_p
             for name in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_analyze_batch",
-                         "kohler_analyze_host", "kohler_stream_status", "kohler_release"):
+                         "kohler_analyze_host", "kohler_stream_status", "kohler_release", "kohler_segment"):
                 getattr(L, name).restype = i
             if hasattr(L, "kohler_server_create"):
                 L.kohler_server_create.argtypes = [p, i32, i32, ctypes.c_size_t, i32]
@@ -209,6 +210,31 @@ def analyze_host(img, M: int, max_k: int):
                                      sumc.ctypes.data, c.ctypes.data, ts.ctypes.data, cnt.ctypes.data,
                                      t0.ctypes.data), "kohler_analyze_host")
     return card, sumc, c, ts[:max_k], int(cnt[0]), int(t0[0])
+
+
+def segment(img: torch.Tensor, M: int, thresholds: torch.Tensor, count: torch.Tensor = None, *, out=None,
+            stream=None) -> torch.Tensor:
+    """The image segmented by `thresholds` (device int32 tensor, any order; entries outside
+    [0, M[ ignored; `count`: device int32 scalar, use only its first entries): every pixel
+    becomes the mean value of its class, rounded half up.  Returns `out` (same shape and
+    dtype as `img`, allocated if not given).  A pixel >= M shows up in stream_status."""
+    if not img.is_cuda:
+        raise ValueError("image must be on the GPU")
+    code = _dtype_code(img)
+    ptr, w, h, pitch = _image(img)
+    ts = thresholds.to(device=img.device, dtype=torch.int32).contiguous()
+    if out is None:
+        out = torch.empty_like(img)
+    optr, ow, oh, opitch = _image(out)
+    if (ow, oh) != (w, h) or out.dtype != img.dtype:
+        raise ValueError("out must match the image's shape and dtype")
+    cptr = None
+    if count is not None:
+        count = count.to(device=img.device, dtype=torch.int32)
+        cptr = count.data_ptr()
+    _check(lib().kohler_segment(ptr, code, w, h, pitch, M, ts.data_ptr() if ts.numel() else None, cptr, ts.numel(),
+                                optr, opitch, _stream(stream)), "kohler_segment")
+    return out
 
 
 def stream_status(stream=None) -> int:

@@ -428,6 +428,14 @@ int validate_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t
 }  // namespace
 
 namespace kohler {
+int stream_sticky(cudaStream_t stream, unsigned** sticky) {
+  Workspace* ws = nullptr;
+  const int rc = get_workspace(stream, 1, 128, cand_ints(2), &ws);
+  if (rc) return rc;
+  *sticky = ws->sticky;
+  return KOHLER_OK;
+}
+
 int launch_images(const kohler_image* imgs, int n, kohler_dtype dt, int M, const int* out_index, const OutSpec& o,
                   cudaStream_t stream) {
   int rc = validate_batch(imgs, n, dt, M, KOHLER_N4);
@@ -545,6 +553,7 @@ int kohler_release(void) {
     }
   }
   release_host_path(dev);
+  kohler::release_segment(dev);
   return KOHLER_OK;
 }
 

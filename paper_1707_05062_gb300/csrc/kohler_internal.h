@@ -23,4 +23,11 @@ struct OutSpec {
 int launch_images(const kohler_image* imgs, int n, kohler_dtype dt, int M, const int* out_index, const OutSpec& o,
                   cudaStream_t stream);
 
+// The error word of `stream` that kohler_stream_status reads (the stream's
+// workspace is created if needed).
+int stream_sticky(cudaStream_t stream, unsigned** sticky);
+
+// Frees the segmentation scratch of every stream of device `dev`.
+void release_segment(int dev);
+
 }  // namespace kohler

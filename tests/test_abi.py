@@ -31,7 +31,7 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_submit", "kohler_poll",
                      "kohler_analyze_batch", "kohler_analyze_host", "kohler_server_create", "kohler_server_destroy",
-                     "kohler_strerror", "kohler_stream_status"):
+                     "kohler_strerror", "kohler_stream_status", "kohler_segment"):
         assert required in names
 
 
@@ -72,3 +72,15 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(k, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         k.lib()
+
+
+def test_segment_argument_errors_without_gpu(lib_path):
+    L = ctypes.CDLL(lib_path)
+    L.kohler_segment.restype = ctypes.c_int
+    p, i64, i32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+    L.kohler_segment.argtypes = [p, i, i64, i64, i64, i32, p, p, i32, p, i64, p]
+    assert L.kohler_segment(None, 1, 8, 8, 8, 256, None, None, 0, 4096, 8, None) == -1   # no image
+    assert L.kohler_segment(1024, 1, 8, 8, 8, 256, None, None, 0, None, 8, None) == -1   # no output
+    assert L.kohler_segment(1024, 1, 8, 8, 8, 300, None, None, 0, 4096, 8, None) == -1   # M > 256 for uint8
+    assert L.kohler_segment(1024, 1, 8, 8, 4, 256, None, None, 0, 4096, 8, None) == -1   # pitch < width
+    assert L.kohler_segment(1024, 1, 8, 8, 8, 256, None, None, 3, 4096, 8, None) == -1   # thresholds missing
