@@ -45,9 +45,19 @@ struct SegParams {
   unsigned* sticky;            // the stream's error word read by kohler_stream_status
   unsigned char* out;          // output image (same type as img)
   int64_t out_pitch;
+  unsigned long long* part;    // [kSegCopies][M] copies of the counts that blocks spread their merges over
+  int32_t vec;                 // every row of img and out starts 16-byte aligned
 };
 
 constexpr unsigned kSegErrRange = 1u;  // same bit as the curve kernels' range error
+constexpr int kUnroll = 4;             // 16-byte chunks of a row in flight per lane
+constexpr int kSegCopies = 8;          // global copies of the level counts (block b adds into copy b % 8)
+
+// Programmatic dependent launch (both no-ops without the launch attribute):
+// let the next kernel of the stream start, and wait for the previous one to
+// finish (and its writes to be visible).
+__device__ __forceinline__ void pdl_allow() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <int ELEM>
 __device__ __forceinline__ uint32_t elem_at(const unsigned char* row, int x) {
@@ -150,22 +160,66 @@ __device__ void seg_table(const SegParams& p, uint32_t* sh) {
   }
 }
 
-// Pixels per grey level.  Warps take rows; a row is read in 16-byte chunks when
-// its start is 16-byte aligned, else element by element.
-template <int ELEM>
+// Walks the image as 16-byte chunks, flat over rows (rows must start 16-byte
+// aligned: `vec`), kUnroll chunks in flight per thread, calling chunk(q, y, c)
+// for chunk c of row y; then the elements no chunk covers (each row's tail, or
+// every element when the rows are not aligned) one by one, calling elem(y, x).
+template <int ELEM, class Chunk, class Elem>
+__device__ __forceinline__ void seg_walk(const SegParams& p, Chunk chunk, Elem elem) {
+  const uint32_t G = gridDim.x * blockDim.x, tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t cpr = p.vec ? (uint32_t)(p.W * ELEM / 16) : 0u;  // chunks per row
+  const uint32_t T = (uint32_t)p.H * cpr;                          // the host keeps this below 2^31
+  for (uint32_t i0 = tid; i0 < T; i0 += G * kUnroll) {
+    uint4 q[kUnroll];
+    uint32_t y[kUnroll], c[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint32_t i = i0 + (uint32_t)u * G;
+      y[u] = i / max(cpr, 1u);
+      c[u] = i - y[u] * cpr;
+      if (i < T) q[u] = __ldg(reinterpret_cast<const uint4*>(p.img + (int64_t)y[u] * p.pitch) + c[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u)
+      if (i0 + (uint32_t)u * G < T) chunk(q[u], y[u], c[u]);
+  }
+  const int x0 = (int)(cpr * 16 / ELEM);  // first element of a row no chunk covers
+  const int tw = p.W - x0;
+  if (tw > 0) {
+    const int64_t S = (int64_t)p.H * tw;
+    for (int64_t i = tid; i < S; i += G) {
+      const int64_t yy = i / tw;
+      elem((int)yy, x0 + (int)(i - yy * tw));
+    }
+  }
+}
+
+// Pixels per grey level: every block counts its share of the image in shared
+// memory (per-lane copies for uint8, one copy for uint16 up to kSegSmemBins
+// levels; beyond that straight into the global counts) and adds its counts
+// into one of kSegCopies global copies (fewer blocks add into the same word).
+// The last block adds the copies up and builds the class table.
+//
+// Launched after another kernel of this library it may start early: it only
+// reads the image before griddepcontrol.wait (the library's kernels never write
+// images that a later call reads, except k_seg_map, which does not let its
+// successor start early), and it waits before its first global write.
+template <int ELEM, bool CHECK>
 __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
   extern __shared__ __align__(16) uint32_t sh_bins[];  // the bins, then the table block's scratch
   __shared__ unsigned sh_last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int M = p.M;
   const bool smem = ELEM == 1 || M <= kSegSmemBins;
   const int nbins = ELEM == 1 ? 256 * 32 : (smem ? M : 0);
   for (int k = threadIdx.x; k < nbins; k += blockDim.x) sh_bins[k] = 0u;
   __syncthreads();
+  pdl_allow();
+  if (!smem) pdl_wait();  // global bins: wait before the first global write
   uint32_t vmax = 0;
   const uint32_t vclamp = (uint32_t)(M - 1);
   auto add = [&](uint32_t v) {
-    vmax = max(vmax, v);
+    if (CHECK) vmax = max(vmax, v);
     if (ELEM == 1) {
       atomicAdd(&sh_bins[v * 32 + lane], 1u);  // per-lane copy: bank = lane
     } else {
@@ -174,13 +228,9 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
       else atomicAdd(p.cnt + v, 1ull);
     }
   };
-  const int per_chunk = 16 / ELEM;
-  for (int64_t y = (int64_t)blockIdx.x * nw + warp; y < p.H; y += (int64_t)gridDim.x * nw) {
-    const unsigned char* row = p.img + y * p.pitch;
-    if (((uintptr_t)row & 15) == 0) {
-      const int full = p.W / per_chunk;
-      for (int c = lane; c < full; c += 32) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(row) + c);
+  seg_walk<ELEM>(
+      p,
+      [&](const uint4 q, uint32_t, uint32_t) {
         const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -194,25 +244,23 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
             add(w[j] >> 16);
           }
         }
-      }
-      for (int x = full * per_chunk + lane; x < p.W; x += 32) add(elem_at<ELEM>(row, x));
-    } else {
-      for (int x = lane; x < p.W; x += 32) add(elem_at<ELEM>(row, x));
-    }
-  }
-  if (vmax > vclamp) atomicOr(p.err, kSegErrRange);
+      },
+      [&](int y, int x) { add(elem_at<ELEM>(p.img + (int64_t)y * p.pitch, x)); });
+  if (smem) pdl_wait();  // before the first global write
+  if (CHECK && vmax > vclamp) atomicOr(p.err, kSegErrRange);
   __syncthreads();
-  // merge into the global counts
+  // this block's counts, added into its copy
+  unsigned long long* copy = p.part + (size_t)(blockIdx.x % kSegCopies) * M;
   if (ELEM == 1) {
     for (int v = threadIdx.x; v < min(M, 256); v += blockDim.x) {
       uint32_t s = 0;
 #pragma unroll 8
       for (int l = 0; l < 32; ++l) s += sh_bins[v * 32 + ((l + v) & 31)];
-      if (s) atomicAdd(p.cnt + v, (unsigned long long)s);
+      if (s) atomicAdd(copy + v, (unsigned long long)s);
     }
   } else if (smem) {
     for (int v = threadIdx.x; v < M; v += blockDim.x)
-      if (sh_bins[v]) atomicAdd(p.cnt + v, (unsigned long long)sh_bins[v]);
+      if (sh_bins[v]) atomicAdd(copy + v, (unsigned long long)sh_bins[v]);
   }
   __threadfence();
   __syncthreads();
@@ -220,6 +268,21 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
   __syncthreads();
   if (sh_last) {
     __threadfence();
+    if (smem) {  // add up the copies (and clear them for the next call)
+      for (int v = threadIdx.x; v < M; v += blockDim.x) {
+        unsigned long long c[kSegCopies], s = 0;
+#pragma unroll
+        for (int r = 0; r < kSegCopies; ++r) c[r] = __ldcg(p.part + (size_t)r * M + v);
+#pragma unroll
+        for (int r = 0; r < kSegCopies; ++r) {
+          s += c[r];
+          p.part[(size_t)r * M + v] = 0ull;
+        }
+        p.cnt[v] = s;
+      }
+      __threadfence();
+      __syncthreads();
+    }
     seg_table(p, sh_bins);  // 32 + M / 32 words: the launch sizes the buffer for it
   }
 }
@@ -227,12 +290,16 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
 // Output pixels: lut[f(x)], the table in shared memory (uint8: one copy per
 // lane, so lookups never conflict; uint16: one copy of up to kSegSmemBins
 // entries, else read through L1).
+//
+// It writes the caller's output image, so it never lets the next kernel start
+// before it finishes; it waits for k_seg_hist (the table) before anything else.
 template <int ELEM>
 __global__ void __launch_bounds__(kSegThreads) k_seg_map(const SegParams p) {
   extern __shared__ __align__(16) uint32_t sh_lut[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31;
   const int M = p.M;
   const bool smem = ELEM == 1 || M <= kSegSmemBins;
+  pdl_wait();
   if (ELEM == 1) {
     for (int k = threadIdx.x; k < 256 * 32; k += blockDim.x) {
       const int v = k >> 5;
@@ -248,15 +315,9 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_map(const SegParams p) {
     v = min(v, vclamp);
     return smem ? sh_lut[v] : __ldg(p.lut + v);
   };
-  const int per_chunk = 16 / ELEM;
-  for (int64_t y = (int64_t)blockIdx.x * nw + warp; y < p.H; y += (int64_t)gridDim.x * nw) {
-    const unsigned char* row = p.img + y * p.pitch;
-    unsigned char* orow = p.out + y * p.out_pitch;
-    int xs = 0;
-    if ((((uintptr_t)row | (uintptr_t)orow) & 15) == 0) {
-      const int full = p.W / per_chunk;
-      for (int c = lane; c < full; c += 32) {
-        const uint4 q = __ldg(reinterpret_cast<const uint4*>(row) + c);
+  seg_walk<ELEM>(
+      p,
+      [&](const uint4 q, uint32_t y, uint32_t c) {
         uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -268,16 +329,14 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_map(const SegParams p) {
             w[j] = map1(w[j] & 0xffffu) | (map1(w[j] >> 16) << 16);
           }
         }
-        reinterpret_cast<uint4*>(orow)[c] = make_uint4(w[0], w[1], w[2], w[3]);
-      }
-      xs = full * per_chunk;
-    }
-    for (int x = xs + lane; x < p.W; x += 32) {
-      const uint32_t r = map1(elem_at<ELEM>(row, x));
-      if (ELEM == 1) orow[x] = (unsigned char)r;
-      else reinterpret_cast<uint16_t*>(orow)[x] = (uint16_t)r;
-    }
-  }
+        reinterpret_cast<uint4*>(p.out + (int64_t)y * p.out_pitch)[c] = make_uint4(w[0], w[1], w[2], w[3]);
+      },
+      [&](int y, int x) {
+        const uint32_t r = map1(elem_at<ELEM>(p.img + (int64_t)y * p.pitch, x));
+        unsigned char* orow = p.out + (int64_t)y * p.out_pitch;
+        if (ELEM == 1) orow[x] = (unsigned char)r;
+        else reinterpret_cast<uint16_t*>(orow)[x] = (uint16_t)r;
+      });
 }
 
 // Per (device, stream) scratch of the segmentation: counts, class sums, the
@@ -285,6 +344,8 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_map(const SegParams p) {
 struct SegWorkspace {
   void* mem = nullptr;
   int M = 0;
+  bool copies = false;
+  unsigned long long* part = nullptr;
   unsigned long long* cnt = nullptr;
   unsigned long long* cls = nullptr;
   uint32_t* lut = nullptr;
@@ -297,13 +358,13 @@ std::map<std::pair<int, uintptr_t>, SegWorkspace> g_seg;
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int seg_workspace(cudaStream_t stream, int M, SegWorkspace** out) {
+int seg_workspace(cudaStream_t stream, int M, bool copies, SegWorkspace** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOHLER_ERR_NOMEM : KOHLER_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_seg_mu);
   SegWorkspace& w = g_seg[std::make_pair(dev, (uintptr_t)stream)];
-  if (w.mem && w.M >= M) {
+  if (w.mem && w.M >= M && (w.copies || !copies)) {
     *out = &w;
     return KOHLER_OK;
   }
@@ -312,8 +373,11 @@ int seg_workspace(cudaStream_t stream, int M, SegWorkspace** out) {
     cudaFree(w.mem);
     w = SegWorkspace();
   }
+  M = std::max(M, w.M);
+  copies = copies || w.copies;
   const size_t b_cnt = up256((size_t)M * 8), b_cls = up256((size_t)(M + 1) * 16), b_lut = up256((size_t)M * 4);
-  const size_t total = b_cnt + b_cls + b_lut + 256;
+  const size_t b_part = copies ? up256((size_t)kSegCopies * M * 8) : 0;
+  const size_t total = b_cnt + b_cls + b_lut + 256 + b_part;
   void* mem = nullptr;
   e = cudaMalloc(&mem, total);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOHLER_ERR_NOMEM : KOHLER_ERR_CUDA;
@@ -329,6 +393,8 @@ int seg_workspace(cudaStream_t stream, int M, SegWorkspace** out) {
   w.lut = reinterpret_cast<uint32_t*>(c + b_cnt + b_cls);
   w.done = reinterpret_cast<unsigned*>(c + b_cnt + b_cls + b_lut);
   w.err = w.done + 1;
+  w.copies = copies;
+  w.part = reinterpret_cast<unsigned long long*>(c + b_cnt + b_cls + b_lut + 256);
   *out = &w;
   return KOHLER_OK;
 }
@@ -372,8 +438,20 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
   unsigned* sticky = nullptr;
   int rc = kohler::stream_sticky(stream, &sticky);
   if (rc) return rc;
+  // 16-byte chunks when every row of the image and of the output starts aligned
+  // (and the chunk count fits 31 bits); blocks: about kUnroll chunks per thread
+  // per pass, at most two (counting) or four (mapping) blocks per SM
+  const int64_t cpr = width * es / 16;
+  const bool vec = ((((uintptr_t)img | (uintptr_t)out | (uintptr_t)pitch_bytes | (uintptr_t)out_pitch_bytes) & 15) == 0) &&
+                   height * cpr < ((int64_t)1 << 31);
+  const int64_t work = vec ? height * cpr : (height * width + 7) / 8;
+  const int64_t per_block = (int64_t)kSegThreads * kUnroll;
+  const int sms = sm_count();
+  const int grid_h = (int)std::max<int64_t>(1, std::min<int64_t>((work + per_block - 1) / per_block, 2 * sms));
+  const int grid_m = (int)std::max<int64_t>(1, std::min<int64_t>((work + per_block - 1) / per_block, 4 * sms));
   SegWorkspace* w = nullptr;
-  rc = seg_workspace(stream, M, &w);
+  const bool binned = dt == KOHLER_U8 || M <= kSegSmemBins;  // counts per block in shared memory
+  rc = seg_workspace(stream, M, binned, &w);
   if (rc) return rc;
   SegParams p;
   memset(&p, 0, sizeof(p));
@@ -393,10 +471,8 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
   p.sticky = sticky;
   p.out = static_cast<unsigned char*>(out);
   p.out_pitch = out_pitch_bytes;
-  const int nw = kSegThreads / 32;
-  // enough warps for every row, at most two blocks per SM
-  const int64_t want = (height + nw - 1) / nw;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, 2 * sm_count()));
+  p.part = w->part;
+  p.vec = vec ? 1 : 0;
   const bool u8 = dt == KOHLER_U8;
   const bool smem16 = M <= kSegSmemBins;
   const size_t hist_smem = u8 ? 256 * 32 * 4 : (smem16 ? (size_t)M * 4 : 0);
@@ -404,7 +480,9 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
   const size_t table_smem = (size_t)(32 + (M + 31) / 32) * 4;
   const size_t smem_h = std::max(hist_smem, table_smem);
   const size_t smem_m = u8 ? 256 * 32 * 4 : (smem16 ? (size_t)M * 4 : 0);
-  const void* fh = u8 ? (const void*)k_seg_hist<1> : (const void*)k_seg_hist<2>;
+  const bool check = !(u8 && M == 256);  // uint8 values are always below 256
+  const void* fh = u8 ? (check ? (const void*)k_seg_hist<1, true> : (const void*)k_seg_hist<1, false>)
+                      : (const void*)k_seg_hist<2, true>;
   const void* fm = u8 ? (const void*)k_seg_map<1> : (const void*)k_seg_map<2>;
   {  // shared memory above 48 KB (uint16 bins), set once per device
     static std::mutex attr_mu;
@@ -413,15 +491,28 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(attr_mu);
     if (!attr_set[dev]) {
-      for (const void* f : {(const void*)k_seg_hist<1>, (const void*)k_seg_hist<2>, (const void*)k_seg_map<1>,
-                            (const void*)k_seg_map<2>})
+      for (const void* f : {(const void*)k_seg_hist<1, true>, (const void*)k_seg_hist<1, false>,
+                            (const void*)k_seg_hist<2, true>, (const void*)k_seg_map<1>, (const void*)k_seg_map<2>})
         cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       attr_set[dev] = true;
     }
   }
   void* args[] = {&p};
-  cudaError_t e = cudaLaunchKernel(fh, dim3(grid), dim3(kSegThreads), args, smem_h, stream);
-  if (e == cudaSuccess) e = cudaLaunchKernel(fm, dim3(grid), dim3(kSegThreads), args, smem_m, stream);
+  // programmatic dependent launch for both (see the kernels for what each waits for)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid_h);
+  cfg.blockDim = dim3(kSegThreads);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.dynamicSmemBytes = smem_h;
+  cudaError_t e = cudaLaunchKernelExC(&cfg, fh, args);
+  cfg.dynamicSmemBytes = smem_m;
+  cfg.gridDim = dim3(grid_m);
+  if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, fm, args);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOHLER_ERR_NOMEM : KOHLER_ERR_CUDA;
   return KOHLER_OK;
 }
