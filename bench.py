@@ -514,6 +514,19 @@ class _Server:
             raise RuntimeError(f"kohler_submit: {rc}")
         return t.value
 
+    def submit_segment(self, frame, out):
+        ct = self.ct
+        t = ct.c_uint64()
+        while True:
+            rc = self.L.kohler_submit_segment(self.h, frame.ctypes.data, 1, frame.shape[1], frame.shape[0],
+                                              frame.strides[0], out.ctypes.data, out.strides[0], ct.byref(t))
+            if rc != self.K.ERR_BUSY:
+                break
+            time.sleep(0.0002)
+        if rc != 0:
+            raise RuntimeError(f"kohler_submit_segment: {rc}")
+        return t.value
+
     def poll(self, ticket):
         ct = self.ct
         ts = (ct.c_int32 * max(1, self.max_k))()
@@ -645,6 +658,68 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
                               "gpx_s": float(px[:len(sub)].sum()) / (t_b - t_a) / 1e9,
                               "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
                               "call": "kohler_analyze_host per frame"}
+    # (iv) open loop again, every frame also segmented into two classes at its t0
+    # and copied back (the paper's video experiment, Section 4 and Table 2);
+    # outputs in per-resolution rings of pinned buffers, a slot reused only
+    # after its frame was polled
+    ring = 16
+    outs = {r: [torch.empty(frames[r][0].shape, dtype=torch.uint8).pin_memory().numpy() for _ in range(ring)]
+            for r in frames}
+    want_seg = {key: oracle.segment(frames[key[0]][key[1]], 256, [want[key][0]]) for key in want}
+    free = {r: threading.Semaphore(ring) for r in frames}
+    srv = _Server(K, 256, MAX_K)
+    q = queue.Queue()
+    t_base = time.perf_counter() + 0.05
+
+    def producer():
+        used = {r: 0 for r in frames}
+        for j, (r, k) in enumerate(src):
+            target = t_base + arrivals[j]
+            dt = target - time.perf_counter()
+            if dt > 3e-4:
+                time.sleep(dt - 3e-4)
+            while time.perf_counter() < target:
+                pass
+            free[r].acquire()
+            slot = used[r] % ring
+            used[r] += 1
+            q.put((j, srv.submit_segment(frames[r][k], outs[r][slot]), target, r, k, slot))
+
+    # the comparisons run in their own thread, off the poll path; it frees the slot
+    checks = queue.Queue()
+    verdict = [True]
+
+    def checker():
+        while True:
+            item = checks.get()
+            if item is None:
+                return
+            r, k, slot, t0 = item
+            verdict[0] = verdict[0] and t0 == want[(r, k)][0] and np.array_equal(outs[r][slot], want_seg[(r, k)])
+            free[r].release()
+
+    th = threading.Thread(target=producer)
+    tc = threading.Thread(target=checker)
+    tc.start()
+    th.start()
+    lat = []
+    for _ in range(n_frames):
+        j, ticket, t_arr, r, k, slot = q.get()
+        t0, cnt, ts, lat_srv = srv.poll(ticket)
+        lat.append(time.perf_counter() - t_arr)
+        checks.put((r, k, slot, t0))
+    th.join()
+    t_end = time.perf_counter()
+    checks.put(None)
+    tc.join()
+    seg_ok = verdict[0]
+    srv.close()
+    out["segmented_open_loop"] = {"fps_achieved": n_frames / (t_end - t_base),
+                                  "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
+                                  "latency_ms_max": max(lat) * 1e3,
+                                  "latency": "scheduled arrival -> two-class frame in host memory (poll returned)",
+                                  "parity_all_frames": bool(seg_ok),
+                                  "paper_context": "97 frames/s segmented, 502x480 video, i7-4702HQ (Table 2)"}
     out["parity_all_frames"] = ok
     return out
 

@@ -202,6 +202,20 @@ int kohler_server_create(kohler_server** s, int32_t M, int32_t max_k, size_t dev
 int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                   int64_t pitch_bytes, uint64_t* ticket);
 
+/* kohler_submit that also returns the frame segmented into two classes by its
+ * own optimal threshold t0 (Section 4: video frames segmented by the method into
+ * two classes, Table 2; classes C_0 = {f <= t0}, C_1 = {f > t0} of Section 2.1,
+ * each pixel replaced by the mean value of its class, rounded half up, as in
+ * kohler_segment).  host_out: caller-owned host buffer of height rows of
+ * out_pitch_bytes (>= width * element size), written by the server before
+ * kohler_poll reports the frame done; it must stay valid until then and should
+ * be pinned (a pageable buffer makes the copy synchronous in the server thread).
+ * A frame with no threshold (t0 = -1, e.g. constant) comes back as one class:
+ * its mean.  Errors as kohler_submit; a frame with a pixel >= M reports
+ * KOHLER_ERR_RANGE from kohler_poll and host_out is then all zero. */
+int kohler_submit_segment(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                          int64_t pitch_bytes, void* host_out, int64_t out_pitch_bytes, uint64_t* ticket);
+
 /* Result of a ticket: KOHLER_OK (out filled, ticket released), KOHLER_PENDING when
  * timeout_us = 0 and not ready, KOHLER_ERR_TIMEOUT after timeout_us microseconds
  * (timeout_us < 0 waits without limit), KOHLER_ERR_RANGE for a frame with a pixel

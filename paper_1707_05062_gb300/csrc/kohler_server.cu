@@ -43,6 +43,8 @@ struct Frame {
   int status = KOHLER_OK;
   int32_t t0 = -1, count = 0;
   std::vector<int32_t> ts;
+  void* host_out = nullptr;  // kohler_submit_segment: the caller's buffer for the two-class frame
+  int64_t out_pitch = 0;
 };
 
 struct LaunchRec {
@@ -209,6 +211,19 @@ bool kohler_server::launch_ready() {
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt + s, d_cnt + s, 4, cudaMemcpyDeviceToHost, compute);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_t0 + s, d_t0 + s, 4, cudaMemcpyDeviceToHost, compute);
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_status + s, d_status + s, 4, cudaMemcpyDeviceToHost, compute);
+      }
+      // frames that asked for their segmentation: two classes at their own t0
+      // (Section 4), segmented in place on the device, then copied to the
+      // caller's buffer before the launch's done event
+      for (size_t j = 0; rc == KOHLER_OK && j < fr.size() && e == cudaSuccess; ++j) {
+        Frame* f = fr[j];
+        if (!f->host_out) continue;
+        const int es = f->dt == KOHLER_U8 ? 1 : 2;
+        rc = kohler_segment(f->dev, f->dt, f->W, f->H, f->dpitch, M, d_t0 + f->slot, nullptr, 1, f->dev, f->dpitch,
+                            compute);
+        if (rc == KOHLER_OK)
+          e = cudaMemcpy2DAsync(f->host_out, f->out_pitch, f->dev, f->dpitch, f->W * es, f->H, cudaMemcpyDeviceToHost,
+                                compute);
       }
       LaunchRec rec;
       rec.done = get_event();
@@ -383,13 +398,19 @@ int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t d
   return KOHLER_OK;
 }
 
-int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
-                  int64_t pitch_bytes, uint64_t* ticket) {
+}  // extern "C"
+
+namespace {
+// kohler_submit and kohler_submit_segment (host_out non-null: the frame is
+// segmented at its t0 and copied back into host_out).
+int submit_frame(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                 int64_t pitch_bytes, void* host_out, int64_t out_pitch, uint64_t* ticket) {
   if (!s || !host_frame || !ticket || (dt != KOHLER_U8 && dt != KOHLER_U16)) return KOHLER_ERR_ARG;
   if (dt == KOHLER_U8 && s->M > 256) return KOHLER_ERR_ARG;
   const int es = dt == KOHLER_U8 ? 1 : 2;
   if (width < 1 || height < 1 || pitch_bytes < width * es || width > (1 << 30) || height > (1 << 30))
     return KOHLER_ERR_ARG;
+  if (host_out && out_pitch < width * es) return KOHLER_ERR_ARG;
   int prev_dev = 0;
   cudaGetDevice(&prev_dev);
   if (prev_dev != s->device) cudaSetDevice(s->device);
@@ -403,6 +424,8 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
   f->dt = dt;
   f->W = width;
   f->H = height;
+  f->host_out = host_out;
+  f->out_pitch = out_pitch;
   f->dpitch = ((width * es + 127) / 128) * 128;
   f->bytes = (size_t)f->dpitch * height;
   f->t_submit = Clock::now();
@@ -479,6 +502,20 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
   }
   s->cv_work.notify_one();
   return KOHLER_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                  int64_t pitch_bytes, uint64_t* ticket) {
+  return submit_frame(s, host_frame, dt, width, height, pitch_bytes, nullptr, 0, ticket);
+}
+
+int kohler_submit_segment(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                          int64_t pitch_bytes, void* host_out, int64_t out_pitch_bytes, uint64_t* ticket) {
+  if (!host_out) return KOHLER_ERR_ARG;
+  return submit_frame(s, host_frame, dt, width, height, pitch_bytes, host_out, out_pitch_bytes, ticket);
 }
 
 int kohler_poll(kohler_server* s, uint64_t ticket, kohler_result* out, int64_t timeout_us) {

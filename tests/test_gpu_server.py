@@ -46,6 +46,13 @@ class Server:
                                   ctypes.byref(t))
         return rc, t.value
 
+    def submit_segment(self, frame, out):
+        t = ctypes.c_uint64()
+        code = 1 if frame.dtype == np.uint8 else 2
+        rc = self.L.kohler_submit_segment(self.h, frame.ctypes.data, code, frame.shape[1], frame.shape[0],
+                                          frame.strides[0], out.ctypes.data, out.strides[0], ctypes.byref(t))
+        return rc, t.value
+
     def poll(self, ticket, timeout_us=-1):
         ts = (ctypes.c_int32 * MAX_K)()
         res = self.K.KohlerResult()
@@ -182,3 +189,44 @@ def test_destroy_with_frames_in_flight(K):
     for f in frames(6, seed=3):
         assert s.submit(f)[0] == 0
     s.close()  # drains admitted frames, drops queued ones, returns
+
+
+def test_segmented_frames(K):
+    # two-class segmentation at each frame's own t0 (Section 4), copied into the
+    # caller's buffer; mixed with a plain submission and a constant frame (one
+    # class: its mean); uint16 frames on a server with M = 4096
+    scene = synth.VideoScene()
+    cases = [(256, [scene.frame(k, w, h) for k, (w, h) in enumerate([(640, 480), (1920, 1080), (64, 33), (640, 480)])]
+              + [np.full((17, 40), 77, np.uint8)]),
+             (4096, [synth.smooth_image(5, 300, 70, 4096, np.uint16), synth.smooth_image(6, 64, 9, 4096, np.uint16)])]
+    for M, frames in cases:
+        srv = Server(K, M=M)
+        outs = []
+        for f in frames:
+            o = torch.zeros(f.shape, dtype=torch.uint8 if f.dtype == np.uint8 else torch.int16).pin_memory().numpy()
+            outs.append(o.view(np.uint16) if f.dtype == np.uint16 else o)
+        tickets = []
+        for j, (f, o) in enumerate(zip(frames, outs)):
+            rc, t = srv.submit(f) if (M == 256 and j == 3) else srv.submit_segment(f, o)
+            assert rc == 0
+            tickets.append(t)
+        for j, (f, o, t) in enumerate(zip(frames, outs, tickets)):
+            rc, t0, cnt, ts, _ = srv.poll(t)
+            assert rc == 0
+            want_t0 = oracle.analyze(f, M, MAX_K)[5]
+            assert t0 == want_t0
+            if M == 256 and j == 3:
+                assert not o.any()  # plain submission: the buffer is untouched
+            else:
+                assert np.array_equal(o, oracle.segment(f, M, [want_t0])), f"M={M} frame {j}"
+        srv.close()
+
+
+def test_segment_submit_arguments(K):
+    srv = Server(K)
+    f = np.zeros((8, 16), np.uint8)
+    o = np.zeros((8, 8), np.uint8)
+    t = ctypes.c_uint64()
+    assert srv.L.kohler_submit_segment(srv.h, f.ctypes.data, 1, 16, 8, 16, None, 16, ctypes.byref(t)) == K.ERR_ARG
+    assert srv.L.kohler_submit_segment(srv.h, f.ctypes.data, 1, 16, 8, 16, o.ctypes.data, 8, ctypes.byref(t)) == K.ERR_ARG
+    srv.close()
