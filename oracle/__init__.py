@@ -53,7 +53,8 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             p, i64, i32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
-            for name in ("oracle_curve", "oracle_curve_n4", "oracle_curve_alg1"):
+            for name in ("oracle_curve", "oracle_curve_n4", "oracle_curve_alg1", "oracle_curve_n8",
+                         "oracle_curve_n8half", "oracle_curve_n8_alg1"):
                 f = getattr(lib, name)
                 f.argtypes = [p, i, i64, i64, i64, i32, p, p]
                 f.restype = i
@@ -106,6 +107,21 @@ def curve_alg1(img: np.ndarray, M: int):
     return _curve_fn("oracle_curve_alg1", img, M)
 
 
+def curve_n8(img: np.ndarray, M: int):
+    """(card, sumc) over ordered pairs of the full 8-neighbourhood (Eq. 1-2 with N8)."""
+    return _curve_fn("oracle_curve_n8", img, M)
+
+
+def curve_n8half(img: np.ndarray, M: int):
+    """(card, sumc) over the half 8-neighbourhood N8* (right, down, down-right, down-left)."""
+    return _curve_fn("oracle_curve_n8half", img, M)
+
+
+def curve_n8_alg1(img: np.ndarray, M: int):
+    """(card, sumc) by Algorithm 1 over the four N8* translations."""
+    return _curve_fn("oracle_curve_n8_alg1", img, M)
+
+
 def curve_at(img: np.ndarray, M: int, ts):
     """(card, sumc) at the listed thresholds only (N4* pairs)."""
     img, es, w, h, pitch = _image_args(img)
@@ -138,9 +154,13 @@ def thresholds(card: np.ndarray, sumc: np.ndarray, max_k: int):
     return out_t[:max_k].copy(), int(cnt.value), int(t0.value)
 
 
-def analyze(img: np.ndarray, M: int, max_k: int, method: str = "alg1"):
-    """Whole path on the CPU: card, sumc, C(t), ranked thresholds, count, t0."""
-    fn = {"alg1": curve_alg1, "def": curve, "n4": curve_n4}[method]
+def analyze(img: np.ndarray, M: int, max_k: int, method: str = "alg1", nbhd: int = 4):
+    """Whole path on the CPU: card, sumc, C(t), ranked thresholds, count, t0
+    (nbhd 4 or 8: the 4- or 8-neighbourhood)."""
+    if nbhd == 8:
+        fn = {"alg1": curve_n8_alg1, "def": curve_n8half, "n8": curve_n8}[method]
+    else:
+        fn = {"alg1": curve_alg1, "def": curve, "n4": curve_n4}[method]
     card, sumc = fn(img, M)
     c = normalise(card, sumc)
     ts, cnt, t0 = thresholds(card, sumc, max_k)

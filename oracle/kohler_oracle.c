@@ -28,6 +28,9 @@
  *   oracle_curve_alg1  Algorithm 1 (per image line, per neighbour of N4*, add the
  *                      contribution of the pair to every t in [min, max-1]),
  *                      with per-thread accumulators summed at the end (Section 3.3).
+ * oracle_curve_n8, oracle_curve_n8half and oracle_curve_n8_alg1 are the same three
+ * routes with the 8-neighbourhood (ordered N8, half neighbourhood N8* = right,
+ * down, down-right, down-left, and Algorithm 1 over the four N8* translations).
  * oracle_thresholds selects the local maxima of C (Section 2.1, text after Eq. 4
  * and Fig. 1) and the optimal threshold t0 of Eq. 4 with exact rational
  * comparisons.
@@ -170,6 +173,126 @@ int oracle_curve_alg1(const void* img, int elem_size, int64_t W, int64_t H, int6
         for (int64_t j = 0; j + ax < W; ++j) {
           uint64_t cur = pixel(img, elem_size, pitch, j, i);
           uint64_t nb = pixel(img, elem_size, pitch, j + ax, i + ay);
+          uint64_t mini = cur < nb ? cur : nb, maxi = cur < nb ? nb : cur;
+          for (uint64_t t = mini; t < maxi; ++t) {
+            Ck[t] += min_u64(maxi - t, t - mini);
+            Cardk[t] += 1;
+          }
+        }
+      }
+    }
+#pragma omp critical
+    {
+      if (ok) {
+        for (int32_t t = 0; t < M; ++t) {
+          sumc[t] += Ck[t];
+          card[t] += Cardk[t];
+        }
+      } else {
+        failed = 1;
+      }
+    }
+    free(Ck);
+    free(Cardk);
+  }
+  return failed ? ORACLE_ERR_ARG : ORACLE_OK;
+}
+
+/* The 8-neighbourhood (Section 2: the method is stated for the 4-neighbourhood
+ * and the text notes that the 8- (or 6-) neighbourhood gives insignificant
+ * differences).  The definitions are the same with N8 in place of N4 in Eq. 1:
+ * x1 one of the eight neighbours of x0, the diagonals included. */
+static const int n8_dx[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+static const int n8_dy[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+
+/* Eq. 1-2 literally over ordered pairs of the full 8-neighbourhood. */
+int oracle_curve_n8(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                    uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t t = 0; t < M; ++t) {
+    uint64_t n = 0, s = 0;
+    for (int64_t y = 0; y < H; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        uint64_t f0 = pixel(img, elem_size, pitch, x, y);
+        for (int k = 0; k < 8; ++k) {
+          int64_t x1 = x + n8_dx[k], y1 = y + n8_dy[k];
+          if (x1 < 0 || x1 >= W || y1 < 0 || y1 >= H) continue;
+          uint64_t f1 = pixel(img, elem_size, pitch, x1, y1);
+          if (f0 <= (uint64_t)t && (uint64_t)t < f1) {
+            n += 1;
+            s += min_u64(f1 - (uint64_t)t, (uint64_t)t - f0);
+          }
+        }
+      }
+    card[t] = n;
+    sumc[t] = s;
+  }
+  return ORACLE_OK;
+}
+
+/* The half 8-neighbourhood N8* = {right, down, down-right, down-left}: every
+ * unordered 8-neighbour pair exactly once (the argument of Section 3.2, Eq. 7-9,
+ * holds for any symmetric neighbourhood); per threshold, per pair, as
+ * oracle_curve does for N4*. */
+int oracle_curve_n8half(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                        uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+  static const int hdx[4] = {1, 0, 1, -1};
+  static const int hdy[4] = {0, 1, 1, 1};
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t t = 0; t < M; ++t) {
+    uint64_t n = 0, s = 0;
+    for (int64_t y = 0; y < H; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        uint64_t f0 = pixel(img, elem_size, pitch, x, y);
+        for (int k = 0; k < 4; ++k) {
+          int64_t x1 = x + hdx[k], y1 = y + hdy[k];
+          if (x1 < 0 || x1 >= W || y1 >= H) continue;
+          uint64_t f1 = pixel(img, elem_size, pitch, x1, y1);
+          uint64_t lo = f0 < f1 ? f0 : f1, hi = f0 < f1 ? f1 : f0;
+          if (lo <= (uint64_t)t && (uint64_t)t < hi) {
+            n += 1;
+            s += min_u64(hi - (uint64_t)t, (uint64_t)t - lo);
+          }
+        }
+      }
+    card[t] = n;
+    sumc[t] = s;
+  }
+  return ORACLE_OK;
+}
+
+/* Algorithm 1 with the four translations of N8* instead of the two of N4*
+ * (same per-thread accumulators, Section 3.3). */
+int oracle_curve_n8_alg1(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                         uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+  static const int hdx[4] = {1, 0, 1, -1};
+  static const int hdy[4] = {0, 1, 1, 1};
+  for (int32_t t = 0; t < M; ++t) card[t] = sumc[t] = 0;
+  int failed = 0;
+#pragma omp parallel
+  {
+    uint64_t* Ck = (uint64_t*)calloc((size_t)M, sizeof(uint64_t));
+    uint64_t* Cardk = (uint64_t*)calloc((size_t)M, sizeof(uint64_t));
+    int ok = Ck && Cardk;
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < H; ++i) {
+      if (!ok) continue;
+      for (int a = 0; a < 4; ++a) {
+        if (i + hdy[a] >= H) continue;
+        for (int64_t j = 0; j < W; ++j) {
+          int64_t j1 = j + hdx[a];
+          if (j1 < 0 || j1 >= W) continue;
+          uint64_t cur = pixel(img, elem_size, pitch, j, i);
+          uint64_t nb = pixel(img, elem_size, pitch, j1, i + hdy[a]);
           uint64_t mini = cur < nb ? cur : nb, maxi = cur < nb ? nb : cur;
           for (uint64_t t = mini; t < maxi; ++t) {
             Ck[t] += min_u64(maxi - t, t - mini);

@@ -20,20 +20,30 @@ def n4(x, y, w, h):
             yield (xx, yy)
 
 
-def boundary(img, t):
-    """B(t) of Eq. 1 as a list of ordered pairs (x0, x1)."""
+def n8(x, y, w, h):
+    """8-neighbours of (x, y) inside the w x h domain D (the diagonals included)."""
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            xx, yy = x + dx, y + dy
+            if (dx or dy) and 0 <= xx < w and 0 <= yy < h:
+                yield (xx, yy)
+
+
+def boundary(img, t, nbhd=4):
+    """B(t) of Eq. 1 as a list of ordered pairs (x0, x1) of the 4- or 8-neighbourhood."""
     h, w = img.shape
     f = {(x, y): int(img[y, x]) for y in range(h) for x in range(w)}
     c0 = {p for p, v in f.items() if v <= t}
     c1 = {p for p, v in f.items() if v > t}
-    return [(x0, x1) for x0 in sorted(c0) for x1 in n4(x0[0], x0[1], w, h) if x1 in c1], f
+    nb = n8 if nbhd == 8 else n4
+    return [(x0, x1) for x0 in sorted(c0) for x1 in nb(x0[0], x0[1], w, h) if x1 in c1], f
 
 
-def curve(img, M):
+def curve(img, M, nbhd=4):
     """(card, sumc) lists over t in [0, M[ from the literal sets."""
     card, sumc = [], []
     for t in range(M):
-        b, f = boundary(img, t)
+        b, f = boundary(img, t, nbhd)
         card.append(len(b))
         sumc.append(sum(min(f[x1] - t, t - f[x0]) for x0, x1 in b))
     return card, sumc
