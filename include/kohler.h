@@ -51,9 +51,13 @@ extern "C" {
 
 typedef enum { KOHLER_U8 = 1, KOHLER_U16 = 2 } kohler_dtype;
 
-/* Neighbourhood of the boundary pairs (Section 2: N4; 8- and 6-neighbourhoods
- * are mentioned as alternatives but not defined further).  Only N4. */
-typedef enum { KOHLER_N4 = 4 } kohler_nbhd;
+/* Neighbourhood of the boundary pairs (Section 2: the method is stated for N4;
+ * the 8- and 6-neighbourhoods are mentioned as giving insignificant
+ * differences).  KOHLER_N4, and KOHLER_N8: the same definitions (Eq. 1-3) with
+ * x1 one of the eight neighbours of x0, the diagonals included (computed on a
+ * general per-pair route; the frame server is N4 only).  Other values:
+ * KOHLER_ERR_UNSUPPORTED. */
+typedef enum { KOHLER_N4 = 4, KOHLER_N8 = 8 } kohler_nbhd;
 
 typedef enum {
   KOHLER_OK = 0,

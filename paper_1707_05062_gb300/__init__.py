@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libkohler.so")
 
 KOHLER_U8, KOHLER_U16 = 1, 2
 KOHLER_N4 = 4
+KOHLER_N8 = 8
 OK, PENDING = 0, 1
 ERR_ARG, ERR_UNSUPPORTED, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY = -1, -2, -3, -4, -5, -6, -7
 
@@ -127,19 +128,20 @@ def _images(imgs: Sequence[torch.Tensor]):
     return arr, (codes.pop() if codes else KOHLER_U8)
 
 
-def curve(img: torch.Tensor, M: int, *, with_curve: bool = True, stream=None):
+def curve(img: torch.Tensor, M: int, *, with_curve: bool = True, stream=None, nbhd: int = KOHLER_N4):
     """(card, sumc, curve) of one device image: int64[M], int64[M], float64[M] (or None)."""
     dev = img.device
     card = torch.empty(M, dtype=torch.int64, device=dev)
     sumc = torch.empty(M, dtype=torch.int64, device=dev)
     c = torch.empty(M, dtype=torch.float64, device=dev) if with_curve else None
     ptr, w, h, pitch = _image(img)
-    _check(lib().kohler_curve(ptr, _dtype_code(img), w, h, pitch, M, KOHLER_N4, card.data_ptr(), sumc.data_ptr(),
+    _check(lib().kohler_curve(ptr, _dtype_code(img), w, h, pitch, M, nbhd, card.data_ptr(), sumc.data_ptr(),
                               c.data_ptr() if c is not None else None, _stream(stream)), "kohler_curve")
     return card, sumc, c
 
 
-def curve_batch(imgs: Sequence[torch.Tensor], M: int, *, with_curve: bool = True, stream=None):
+def curve_batch(imgs: Sequence[torch.Tensor], M: int, *, with_curve: bool = True, stream=None,
+                nbhd: int = KOHLER_N4):
     """(card, sumc, curve) of n device images: [n, M] each (curve may be None)."""
     n = len(imgs)
     dev = imgs[0].device if n else torch.device("cuda")
@@ -147,7 +149,7 @@ def curve_batch(imgs: Sequence[torch.Tensor], M: int, *, with_curve: bool = True
     card = torch.empty((n, M), dtype=torch.int64, device=dev)
     sumc = torch.empty((n, M), dtype=torch.int64, device=dev)
     c = torch.empty((n, M), dtype=torch.float64, device=dev) if with_curve else None
-    _check(lib().kohler_curve_batch(arr, n, code, M, KOHLER_N4, card.data_ptr(), sumc.data_ptr(),
+    _check(lib().kohler_curve_batch(arr, n, code, M, nbhd, card.data_ptr(), sumc.data_ptr(),
                                     c.data_ptr() if c is not None else None, _stream(stream)), "kohler_curve_batch")
     return card, sumc, c
 
@@ -168,7 +170,7 @@ def thresholds(card: torch.Tensor, sumc: torch.Tensor, max_k: int, *, stream=Non
 
 
 def analyze_batch(imgs: Sequence[torch.Tensor], M: int, max_k: int, *, with_curve: bool = True, stream=None,
-                  out=None):
+                  out=None, nbhd: int = KOHLER_N4):
     """Fused curves and thresholds of n device images (one launch per 128 images).
     Returns (card, sumc, curve, out_t, count, t0); `out` may supply these tensors."""
     n = len(imgs)
@@ -180,13 +182,13 @@ def analyze_batch(imgs: Sequence[torch.Tensor], M: int, max_k: int, *, with_curv
                torch.empty((n, max(max_k, 1)), dtype=torch.int32, device=dev),
                torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev))
     card, sumc, c, out_t, cnt, t0 = out
-    _check(lib().kohler_analyze_batch(arr, n, code, M, KOHLER_N4, max_k, card.data_ptr(), sumc.data_ptr(),
+    _check(lib().kohler_analyze_batch(arr, n, code, M, nbhd, max_k, card.data_ptr(), sumc.data_ptr(),
                                       c.data_ptr() if c is not None else None, out_t.data_ptr(), cnt.data_ptr(),
                                       t0.data_ptr(), _stream(stream)), "kohler_analyze_batch")
     return card, sumc, c, out_t[:, :max_k], cnt, t0
 
 
-def analyze_host(img, M: int, max_k: int):
+def analyze_host(img, M: int, max_k: int, nbhd: int = KOHLER_N4):
     """Whole path from a host image (numpy array or CPU tensor, pinned is fastest) back
     to host results: (card, sumc, curve, thresholds, count, t0) as numpy arrays."""
     import numpy as np
@@ -208,7 +210,7 @@ def analyze_host(img, M: int, max_k: int):
     ts = np.empty(max(max_k, 1), np.int32)
     cnt = np.zeros(1, np.int32)
     t0 = np.zeros(1, np.int32)
-    _check(lib().kohler_analyze_host(ptr, code, w, h, pitch, M, KOHLER_N4, max_k, card.ctypes.data,
+    _check(lib().kohler_analyze_host(ptr, code, w, h, pitch, M, nbhd, max_k, card.ctypes.data,
                                      sumc.ctypes.data, c.ctypes.data, ts.ctypes.data, cnt.ctypes.data,
                                      t0.ctypes.data), "kohler_analyze_host")
     return card, sumc, c, ts[:max_k], int(cnt[0]), int(t0[0])

@@ -137,7 +137,11 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
   return KOHLER_OK;
 }
 
-enum class Pass { HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16 };
+enum class Pass {
+  HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16,
+  // the 8-neighbourhood (general per-pair route)
+  GenericU8N8, GenericU16N8, GlobalU8N8, GlobalU16N8
+};
 
 int bins_for(kohler_dtype dt, int M) { return dt == KOHLER_U8 ? 256 : ((M + 31) / 32) * 32; }
 // Histogram words per workspace slot.
@@ -157,11 +161,15 @@ int check_image(const void* img, kohler_dtype dt, int64_t W, int64_t H, int64_t 
 int check_common(kohler_dtype dt, int32_t M, kohler_nbhd nb) {
   if (dt != KOHLER_U8 && dt != KOHLER_U16) return KOHLER_ERR_ARG;
   if (M < 2 || (dt == KOHLER_U8 && M > 256) || (dt == KOHLER_U16 && M > 65536)) return KOHLER_ERR_ARG;
-  if (nb != KOHLER_N4) return KOHLER_ERR_UNSUPPORTED;
+  if (nb != KOHLER_N4 && nb != KOHLER_N8) return KOHLER_ERR_UNSUPPORTED;
   return KOHLER_OK;
 }
 
-Pass pass_for(const kohler_image& im, kohler_dtype dt, int M) {
+Pass pass_for(const kohler_image& im, kohler_dtype dt, int M, kohler_nbhd nb) {
+  if (nb == KOHLER_N8) {
+    if (dt == KOHLER_U8) return Pass::GenericU8N8;
+    return M > kMaxSmemBins ? Pass::GlobalU16N8 : Pass::GenericU16N8;
+  }
   const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
   const bool aligned16 = (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0);
   if (dt == KOHLER_U8) {
@@ -204,10 +212,14 @@ KernelInfo kernel_for(Pass p, int bins, bool single) {
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16:
       return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
-    case Pass::GenericU8: return {(const void*)k_generic<1, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GenericU16: return {(const void*)k_generic<2, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GlobalU8: return {(const void*)k_generic<1, true>, kGenericWarps * 32, 0};
-    case Pass::GlobalU16: return {(const void*)k_generic<2, true>, kGenericWarps * 32, 0};
+    case Pass::GenericU8: return {(const void*)k_generic<1, false, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16: return {(const void*)k_generic<2, false, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU8: return {(const void*)k_generic<1, true, false>, kGenericWarps * 32, 0};
+    case Pass::GlobalU16: return {(const void*)k_generic<2, true, false>, kGenericWarps * 32, 0};
+    case Pass::GenericU8N8: return {(const void*)k_generic<1, false, true>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16N8: return {(const void*)k_generic<2, false, true>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU8N8: return {(const void*)k_generic<1, true, true>, kGenericWarps * 32, 0};
+    case Pass::GlobalU16N8: return {(const void*)k_generic<2, true, true>, kGenericWarps * 32, 0};
   }
   return {nullptr, 0, 0};
 }
@@ -366,7 +378,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
 int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, int32_t max_k, uint64_t* card,
               uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0,
               cudaStream_t stream, const std::vector<Band>* bands, const int* out_index = nullptr,
-              int32_t* out_status = nullptr) {
+              int32_t* out_status = nullptr, kohler_nbhd nb = KOHLER_N4) {
   const int bins = bins_for(dt, M);
   const int cand_stride = cand_ints(M);
   const int chunk = std::min<int>(kMaxBatch, std::max<int>(1, (int)std::min<int64_t>(
@@ -400,7 +412,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
     std::map<Pass, std::vector<int>> groups;
     std::vector<int> slot_of(cn);
     for (int j = 0; j < cn; ++j) {
-      groups[pass_for(imgs[c0 + j], dt, M)].push_back(j);
+      groups[pass_for(imgs[c0 + j], dt, M, nb)].push_back(j);
       slot_of[j] = j;
     }
     std::vector<Band> sub_bands;
@@ -461,7 +473,7 @@ int kohler_curve_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int
   if (n == 0) return KOHLER_OK;
   if (!card || !sumc) return KOHLER_ERR_ARG;
   return run_batch(imgs, n, dt, M, 0, card, sumc, curve, nullptr, nullptr, nullptr, (cudaStream_t)cuda_stream,
-                   nullptr);
+                   nullptr, nullptr, nullptr, nb);
 }
 
 int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
@@ -472,7 +484,7 @@ int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, i
   if (n == 0) return KOHLER_OK;
   if (!card || !sumc || max_k < 0 || (max_k > 0 && !out_t) || !out_count || !out_t0) return KOHLER_ERR_ARG;
   return run_batch(imgs, n, dt, M, max_k, card, sumc, curve, out_t, out_count, out_t0, (cudaStream_t)cuda_stream,
-                   nullptr);
+                   nullptr, nullptr, nullptr, nb);
 }
 
 int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int32_t M, int32_t max_k,
@@ -677,7 +689,7 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
                      reinterpret_cast<uint64_t*>(dout + o_sumc), reinterpret_cast<double*>(dout + o_curve),
                      max_k > 0 ? reinterpret_cast<int32_t*>(dout + o_t) : nullptr,
                      reinterpret_cast<int32_t*>(dout + o_cnt), reinterpret_cast<int32_t*>(dout + o_t0), h->compute,
-                     band);
+                     band, nullptr, nullptr, nb);
   };
   cudaError_t e = cudaSuccess;
   {
@@ -784,8 +796,9 @@ extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t 
   if (rc) return rc;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   const kohler_image im{img, width, height, pitch_bytes};
-  const Pass pass = pass_for(im, dt, M);
-  if (pass == Pass::GlobalU8 || pass == Pass::GlobalU16) return KOHLER_ERR_ARG;
+  const Pass pass = pass_for(im, dt, M, nb);
+  if (pass == Pass::GlobalU8 || pass == Pass::GlobalU16 || pass == Pass::GlobalU8N8 || pass == Pass::GlobalU16N8)
+    return KOHLER_ERR_ARG;
   const int bins = bins_for(dt, M);
   char* s = static_cast<char*>(scratch);
   // the array keeps the previous call's contents: clear histograms and counters

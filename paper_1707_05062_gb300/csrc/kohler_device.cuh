@@ -1459,8 +1459,11 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
 // Any layout and alignment, uint8 or uint16, M <= bins: one lane per pixel of a
 // 32-pixel strip, walking down rows; three shared-memory updates per pair
 // (H_lo, H_hi, H_s).  With GLOBAL the updates go straight to the image's global
-// histograms (for M too large for shared memory).
-template <int ELEM, bool GLOBAL>
+// histograms (for M too large for shared memory).  N8: the 8-neighbourhood, whose
+// half neighbourhood N8* adds the lower-right and lower-left pairs to the right
+// and lower ones (every unordered 8-neighbour pair once, as Section 3.2 argues
+// for N4*).
+template <int ELEM, bool GLOBAL, bool N8>
 __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
   __shared__ uint64_t scratch[kScratch];
@@ -1508,6 +1511,15 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchP
         const uint32_t nxt = (act && y + 1 < H) ? px(y + 1, x) : 0u;
         uint32_t right = __shfl_down_sync(0xffffffffu, cur, 1);
         if (act && x + 1 < W && lane == 31) right = px(y, x + 1);
+        uint32_t dright = 0u, dleft = 0u;  // lower-right and lower-left neighbours (N8)
+        if (N8) {
+          dright = __shfl_down_sync(0xffffffffu, nxt, 1);
+          dleft = __shfl_up_sync(0xffffffffu, nxt, 1);
+          if (act && y + 1 < H) {
+            if (lane == 31 && x + 1 < W) dright = px(y + 1, x + 1);
+            if (lane == 0 && x > 0) dleft = px(y + 1, x - 1);
+          }
+        }
         if (act) {
           bad |= cur >= (uint32_t)P.M;
           const uint32_t c = min(cur, (uint32_t)P.M - 1);
@@ -1527,6 +1539,10 @@ __global__ void __launch_bounds__(256) k_generic(const __grid_constant__ LaunchP
           };
           if (x + 1 < W) add_pair(right);
           if (y + 1 < H) add_pair(nxt);
+          if (N8 && y + 1 < H) {
+            if (x + 1 < W) add_pair(dright);
+            if (x > 0) add_pair(dleft);
+          }
         }
         cur = nxt;
       }
