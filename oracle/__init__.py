@@ -54,7 +54,8 @@ def _load():
             lib = ctypes.CDLL(build())
             p, i64, i32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
             for name in ("oracle_curve", "oracle_curve_n4", "oracle_curve_alg1", "oracle_curve_n8",
-                         "oracle_curve_n8half", "oracle_curve_n8_alg1"):
+                         "oracle_curve_n8half", "oracle_curve_n8_alg1", "oracle_curve_n6", "oracle_curve_n6half",
+                         "oracle_curve_n6_alg1"):
                 f = getattr(lib, name)
                 f.argtypes = [p, i, i64, i64, i64, i32, p, p]
                 f.restype = i
@@ -122,6 +123,23 @@ def curve_n8_alg1(img: np.ndarray, M: int):
     return _curve_fn("oracle_curve_n8_alg1", img, M)
 
 
+def curve_n6(img: np.ndarray, M: int):
+    """(card, sumc) over ordered pairs of the full hexagonal 6-neighbourhood (odd rows
+    shifted half a pixel right)."""
+    return _curve_fn("oracle_curve_n6", img, M)
+
+
+def curve_n6half(img: np.ndarray, M: int):
+    """(card, sumc) over the half 6-neighbourhood N6* (right, down, and down-left on
+    even rows or down-right on odd rows)."""
+    return _curve_fn("oracle_curve_n6half", img, M)
+
+
+def curve_n6_alg1(img: np.ndarray, M: int):
+    """(card, sumc) by Algorithm 1 over the three N6* translations."""
+    return _curve_fn("oracle_curve_n6_alg1", img, M)
+
+
 def curve_at(img: np.ndarray, M: int, ts):
     """(card, sumc) at the listed thresholds only (N4* pairs)."""
     img, es, w, h, pitch = _image_args(img)
@@ -156,9 +174,11 @@ def thresholds(card: np.ndarray, sumc: np.ndarray, max_k: int):
 
 def analyze(img: np.ndarray, M: int, max_k: int, method: str = "alg1", nbhd: int = 4):
     """Whole path on the CPU: card, sumc, C(t), ranked thresholds, count, t0
-    (nbhd 4 or 8: the 4- or 8-neighbourhood)."""
+    (nbhd 4, 6 or 8: the 4-, hexagonal 6- or 8-neighbourhood)."""
     if nbhd == 8:
         fn = {"alg1": curve_n8_alg1, "def": curve_n8half, "n8": curve_n8}[method]
+    elif nbhd == 6:
+        fn = {"alg1": curve_n6_alg1, "def": curve_n6half, "n6": curve_n6}[method]
     else:
         fn = {"alg1": curve_alg1, "def": curve, "n4": curve_n4}[method]
     card, sumc = fn(img, M)

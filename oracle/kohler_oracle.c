@@ -31,6 +31,8 @@
  * oracle_curve_n8, oracle_curve_n8half and oracle_curve_n8_alg1 are the same three
  * routes with the 8-neighbourhood (ordered N8, half neighbourhood N8* = right,
  * down, down-right, down-left, and Algorithm 1 over the four N8* translations).
+ * oracle_curve_n6, oracle_curve_n6half and oracle_curve_n6_alg1 do the same with
+ * the 6-neighbourhood of a hexagonal grid (odd rows shifted half a pixel right).
  * oracle_thresholds selects the local maxima of C (Section 2.1, text after Eq. 4
  * and Fig. 1) and the optimal threshold t0 of Eq. 4 with exact rational
  * comparisons.
@@ -293,6 +295,138 @@ int oracle_curve_n8_alg1(const void* img, int elem_size, int64_t W, int64_t H, i
           if (j1 < 0 || j1 >= W) continue;
           uint64_t cur = pixel(img, elem_size, pitch, j, i);
           uint64_t nb = pixel(img, elem_size, pitch, j1, i + hdy[a]);
+          uint64_t mini = cur < nb ? cur : nb, maxi = cur < nb ? nb : cur;
+          for (uint64_t t = mini; t < maxi; ++t) {
+            Ck[t] += min_u64(maxi - t, t - mini);
+            Cardk[t] += 1;
+          }
+        }
+      }
+    }
+#pragma omp critical
+    {
+      if (ok) {
+        for (int32_t t = 0; t < M; ++t) {
+          sumc[t] += Ck[t];
+          card[t] += Cardk[t];
+        }
+      } else {
+        failed = 1;
+      }
+    }
+    free(Ck);
+    free(Cardk);
+  }
+  return failed ? ORACLE_ERR_ARG : ORACLE_OK;
+}
+
+/* The 6-neighbourhood of a hexagonal grid (Section 2 names it beside the 8-
+ * neighbourhood).  The grid is stored row by row with every odd row (0-based)
+ * shifted half a pixel to the right, so that the pixel (x, y) touches:
+ *   (x - 1, y), (x + 1, y), and in the rows y - 1 and y + 1
+ *   columns x - 1 and x when y is even, columns x and x + 1 when y is odd.
+ * The relation is symmetric: an even-row pixel's lower-left neighbour has it as
+ * its upper-right one.  Eq. 1-3 are unchanged with N6 in place of N4. */
+static void n6_neighbour(int64_t x, int64_t y, int k, int64_t* x1, int64_t* y1) {
+  /* k = 0..5: right, left, up (same column), down (same column), up-shifted,
+   * down-shifted; the shifted column is x - 1 on even rows, x + 1 on odd rows */
+  int64_t shift = (y % 2 == 0) ? -1 : 1;
+  static const int dx0[6] = {1, -1, 0, 0, 0, 0};
+  static const int dy0[6] = {0, 0, -1, 1, -1, 1};
+  *x1 = x + dx0[k] + (k >= 4 ? shift : 0);
+  *y1 = y + dy0[k];
+}
+
+/* Eq. 1-2 literally over ordered pairs of the full 6-neighbourhood. */
+int oracle_curve_n6(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                    uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t t = 0; t < M; ++t) {
+    uint64_t n = 0, s = 0;
+    for (int64_t y = 0; y < H; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        uint64_t f0 = pixel(img, elem_size, pitch, x, y);
+        for (int k = 0; k < 6; ++k) {
+          int64_t x1, y1;
+          n6_neighbour(x, y, k, &x1, &y1);
+          if (x1 < 0 || x1 >= W || y1 < 0 || y1 >= H) continue;
+          uint64_t f1 = pixel(img, elem_size, pitch, x1, y1);
+          if (f0 <= (uint64_t)t && (uint64_t)t < f1) {
+            n += 1;
+            s += min_u64(f1 - (uint64_t)t, (uint64_t)t - f0);
+          }
+        }
+      }
+    card[t] = n;
+    sumc[t] = s;
+  }
+  return ORACLE_OK;
+}
+
+/* The half 6-neighbourhood N6* = {right, down, down-shifted}: every unordered
+ * 6-neighbour pair once (Section 3.2's argument, Eq. 7-9, for a symmetric
+ * neighbourhood); per threshold, per pair. */
+int oracle_curve_n6half(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                        uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+  static const int half[3] = {0, 3, 5};  /* right, down, down-shifted in n6_neighbour */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t t = 0; t < M; ++t) {
+    uint64_t n = 0, s = 0;
+    for (int64_t y = 0; y < H; ++y)
+      for (int64_t x = 0; x < W; ++x) {
+        uint64_t f0 = pixel(img, elem_size, pitch, x, y);
+        for (int k = 0; k < 3; ++k) {
+          int64_t x1, y1;
+          n6_neighbour(x, y, half[k], &x1, &y1);
+          if (x1 < 0 || x1 >= W || y1 >= H) continue;
+          uint64_t f1 = pixel(img, elem_size, pitch, x1, y1);
+          uint64_t lo = f0 < f1 ? f0 : f1, hi = f0 < f1 ? f1 : f0;
+          if (lo <= (uint64_t)t && (uint64_t)t < hi) {
+            n += 1;
+            s += min_u64(hi - (uint64_t)t, (uint64_t)t - lo);
+          }
+        }
+      }
+    card[t] = n;
+    sumc[t] = s;
+  }
+  return ORACLE_OK;
+}
+
+/* Algorithm 1 over the three translations of N6*: line i against itself moved
+ * one column (right pairs), against line i + 1 (down pairs) and against line
+ * i + 1 moved one column left (i even) or right (i odd) (Section 3.3 accumulators). */
+int oracle_curve_n6_alg1(const void* img, int elem_size, int64_t W, int64_t H, int64_t pitch, int32_t M,
+                         uint64_t* card, uint64_t* sumc) {
+  int rc = check_args(img, elem_size, W, H, pitch, M);
+  if (rc) return rc;
+  if (!card || !sumc) return ORACLE_ERR_ARG;
+  for (int32_t t = 0; t < M; ++t) card[t] = sumc[t] = 0;
+  int failed = 0;
+#pragma omp parallel
+  {
+    uint64_t* Ck = (uint64_t*)calloc((size_t)M, sizeof(uint64_t));
+    uint64_t* Cardk = (uint64_t*)calloc((size_t)M, sizeof(uint64_t));
+    int ok = Ck && Cardk;
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < H; ++i) {
+      if (!ok) continue;
+      int64_t shift = (i % 2 == 0) ? -1 : 1;
+      const int64_t adx[3] = {1, 0, shift};
+      const int64_t ady[3] = {0, 1, 1};
+      for (int a = 0; a < 3; ++a) {
+        if (i + ady[a] >= H) continue;
+        for (int64_t j = 0; j < W; ++j) {
+          int64_t j1 = j + adx[a];
+          if (j1 < 0 || j1 >= W) continue;
+          uint64_t cur = pixel(img, elem_size, pitch, j, i);
+          uint64_t nb = pixel(img, elem_size, pitch, j1, i + ady[a]);
           uint64_t mini = cur < nb ? cur : nb, maxi = cur < nb ? nb : cur;
           for (uint64_t t = mini; t < maxi; ++t) {
             Ck[t] += min_u64(maxi - t, t - mini);

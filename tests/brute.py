@@ -29,13 +29,30 @@ def n8(x, y, w, h):
                 yield (xx, yy)
 
 
+def n6(x, y, w, h):
+    """Neighbours of (x, y) on a hexagonal grid stored row by row, odd rows shifted
+    half a pixel to the right: the pixel's centre sits at column x + (y mod 2) / 2,
+    and its neighbours are the pixels of rows y - 1, y, y + 1 whose centres lie at
+    distance exactly 1 (same row) or whose centres are half a column away (rows
+    above and below)."""
+    cx = Fraction(2 * x + (y % 2), 2)
+    for yy in (y - 1, y, y + 1):
+        if not 0 <= yy < h:
+            continue
+        for xx in range(max(0, x - 1), min(w, x + 2)):
+            d = Fraction(2 * xx + (yy % 2), 2) - cx
+            if (yy == y and abs(d) == 1) or (yy != y and abs(d) == Fraction(1, 2)):
+                yield (xx, yy)
+
+
 def boundary(img, t, nbhd=4):
-    """B(t) of Eq. 1 as a list of ordered pairs (x0, x1) of the 4- or 8-neighbourhood."""
+    """B(t) of Eq. 1 as a list of ordered pairs (x0, x1) of the 4-, hexagonal 6- or
+    8-neighbourhood."""
     h, w = img.shape
     f = {(x, y): int(img[y, x]) for y in range(h) for x in range(w)}
     c0 = {p for p, v in f.items() if v <= t}
     c1 = {p for p, v in f.items() if v > t}
-    nb = n8 if nbhd == 8 else n4
+    nb = {4: n4, 6: n6, 8: n8}[nbhd]
     return [(x0, x1) for x0 in sorted(c0) for x1 in nb(x0[0], x0[1], w, h) if x1 in c1], f
 
 
