@@ -20,8 +20,10 @@ At N = 1 the same line carries "forms": the batched form (one launch over a
 against one launch per image on the same resident images, and the served form
 (2000 Poisson-arriving video frames of mixed resolution through the
 continuous-batching server: p50/p99 latency, closed-loop frames/s, and one
-synchronous host call per frame for comparison).  Every form checks its
-results against the oracle.
+synchronous host call per frame for comparison), segmentation of the 18-Mpixel
+images by their ranked thresholds, and the whole path with the 8- and hexagonal
+6-neighbourhoods beside the 4-neighbourhood.  Every form checks its results
+against the oracle.
 """
 from __future__ import annotations
 
@@ -159,15 +161,27 @@ def measured_peak_hbm():
         return 6800.0, "fallback"
 
 
+# Device sources each profiled kernel is compiled from (its pass and the common
+# epilogue); a change to another pass leaves its counters valid.
+KERNEL_SOURCES = {"k_u8h": ("kohler_common.cuh", "kohler_u8h.cuh")}
+
+
+def device_source_digest(kernel: str) -> str:
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1707_05062_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary of this kernel and
-    workload, if it was taken on the current device source (else None)."""
+    workload, if it was taken on the kernel's current device source (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
-    src = os.path.join(ROOT, "paper_1707_05062_gb300", "csrc", "kohler_device.cuh")
     try:
         text = open(path).read()
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except OSError:
+        digest = device_source_digest(kernel)
+    except (OSError, KeyError):
         return None
     traffic = source = None
     for line in text.splitlines():
@@ -767,6 +781,41 @@ def form_segment(K, torch, dev, peak, n_pool=6):
             "launch": f"CUDA-graph replays of {n_pool} images"}
 
 
+def form_nbhd(K, torch, dev, peak, n_pool=6):
+    """The whole path (curve + thresholds) of the 18-Mpixel images with the 8- and
+    the hexagonal 6-neighbourhood, beside the 4-neighbourhood, as CUDA-graph
+    replays cycling n_pool images (more bytes than L2); one image of each checked
+    against the oracle."""
+    import oracle
+    import synth
+
+    pool_np = synth.voronoi_18mp_pool(n_pool)
+    H, W = pool_np[0].shape
+    px = W * H
+    imgs = [torch.from_numpy(im).to(dev) for im in pool_np]
+    out = {"workload": f"{W}x{H} uint8 Voronoi images, M = 256", "launch": f"CUDA-graph replays of {n_pool} images"}
+    for nb in (4, 8, 6):
+        res = [K.analyze_batch([im], 256, 16, nbhd=nb) for im in imgs]
+        torch.cuda.synchronize(dev)
+
+        def run(s, nb=nb, res=res):
+            for j in range(n_pool):
+                K.analyze_batch([imgs[j]], 256, 16, out=res[j], stream=s, nbhd=nb)
+
+        g, st = _graph_of(torch, dev, run)
+        t = _time_graph(torch, g, st, 20) / n_pool
+        if K.stream_status(st) != K.OK:
+            raise RuntimeError(f"N{nb}: a launch reported an error")
+        want = oracle.analyze(pool_np[0], 256, 16, nbhd=nb)
+        got = (res[0][0][0].cpu().numpy().view(np.uint64), res[0][1][0].cpu().numpy().view(np.uint64),
+               res[0][2][0].cpu().numpy(), res[0][3][0].cpu().numpy(), int(res[0][4][0]), int(res[0][5][0]))
+        ok = all(np.array_equal(got[k], want[k]) for k in range(4)) and got[4:] == want[4:]
+        pairs = {4: 2, 8: 4, 6: 3}[nb]
+        out[f"N{nb}"] = {"ms": t * 1e3, "gpx_s": px / t / 1e9, "gpairs_s": pairs * px / t / 1e9,
+                         "hbm_frac": px / t / 1e9 / peak, "parity_spot_check": bool(ok)}
+    return out
+
+
 def run_forms(args, K, torch, dev, peak):
     forms = {}
     names = [x for x in args.forms.split(",") if x]
@@ -793,6 +842,8 @@ def run_forms(args, K, torch, dev, peak):
                 forms[name] = form_served(K, torch, dev)
             elif name == "segment":
                 forms[name] = form_segment(K, torch, dev, peak)
+            elif name == "nbhd":
+                forms[name] = form_nbhd(K, torch, dev, peak)
             else:
                 forms[name] = {"error": "unknown form"}
         except Exception as e:  # a failing form is reported, not hidden
@@ -846,7 +897,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served,segment",
+    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served,segment,nbhd",
                     help="comma list of extra forms reported in the same line (N = 1 only); empty for none")
     args = ap.parse_args(argv)
     if args.warmup < 3:

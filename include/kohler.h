@@ -53,11 +53,17 @@ typedef enum { KOHLER_U8 = 1, KOHLER_U16 = 2 } kohler_dtype;
 
 /* Neighbourhood of the boundary pairs (Section 2: the method is stated for N4;
  * the 8- and 6-neighbourhoods are mentioned as giving insignificant
- * differences).  KOHLER_N4, and KOHLER_N8: the same definitions (Eq. 1-3) with
- * x1 one of the eight neighbours of x0, the diagonals included (computed on a
- * general per-pair route; the frame server is N4 only).  Other values:
- * KOHLER_ERR_UNSUPPORTED. */
-typedef enum { KOHLER_N4 = 4, KOHLER_N8 = 8 } kohler_nbhd;
+ * differences).  The same definitions (Eq. 1-3) hold with x1 one of:
+ *   KOHLER_N4  the four horizontal and vertical neighbours of x0;
+ *   KOHLER_N8  the eight neighbours, the diagonals included;
+ *   KOHLER_N6  the six neighbours of a hexagonal grid stored row by row with
+ *              every odd row (0-based, counted from the image's first row)
+ *              shifted half a pixel to the right: the left and right pixels,
+ *              and in the rows above and below columns x - 1 and x on an even
+ *              row, x and x + 1 on an odd row.
+ * N8 and N6 are computed on a general per-pair route; the frame server is N4
+ * only.  Other values: KOHLER_ERR_UNSUPPORTED. */
+typedef enum { KOHLER_N4 = 4, KOHLER_N6 = 6, KOHLER_N8 = 8 } kohler_nbhd;
 
 typedef enum {
   KOHLER_OK = 0,

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libkohler.so")
 
 KOHLER_U8, KOHLER_U16 = 1, 2
 KOHLER_N4 = 4
+KOHLER_N6 = 6
 KOHLER_N8 = 8
 OK, PENDING = 0, 1
 ERR_ARG, ERR_UNSUPPORTED, ERR_RANGE, ERR_NOMEM, ERR_CUDA, ERR_TIMEOUT, ERR_BUSY = -1, -2, -3, -4, -5, -6, -7

@@ -139,9 +139,14 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
 
 enum class Pass {
   HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16,
-  // the 8-neighbourhood (general per-pair route)
-  GenericU8N8, GenericU16N8, GlobalU8N8, GlobalU16N8
+  // the 8- and hexagonal 6-neighbourhoods (general per-pair route)
+  GenericU8N8, GenericU16N8, GlobalU16N8, GenericU8N6, GenericU16N6, GlobalU16N6
 };
+
+// Passes that add straight to the global histograms (M above the shared-memory bins).
+bool is_global(Pass p) {
+  return p == Pass::GlobalU8 || p == Pass::GlobalU16 || p == Pass::GlobalU16N8 || p == Pass::GlobalU16N6;
+}
 
 int bins_for(kohler_dtype dt, int M) { return dt == KOHLER_U8 ? 256 : ((M + 31) / 32) * 32; }
 // Histogram words per workspace slot.
@@ -161,7 +166,7 @@ int check_image(const void* img, kohler_dtype dt, int64_t W, int64_t H, int64_t 
 int check_common(kohler_dtype dt, int32_t M, kohler_nbhd nb) {
   if (dt != KOHLER_U8 && dt != KOHLER_U16) return KOHLER_ERR_ARG;
   if (M < 2 || (dt == KOHLER_U8 && M > 256) || (dt == KOHLER_U16 && M > 65536)) return KOHLER_ERR_ARG;
-  if (nb != KOHLER_N4 && nb != KOHLER_N8) return KOHLER_ERR_UNSUPPORTED;
+  if (nb != KOHLER_N4 && nb != KOHLER_N6 && nb != KOHLER_N8) return KOHLER_ERR_UNSUPPORTED;
   return KOHLER_OK;
 }
 
@@ -169,6 +174,10 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M, kohler_nbhd nb) {
   if (nb == KOHLER_N8) {
     if (dt == KOHLER_U8) return Pass::GenericU8N8;
     return M > kMaxSmemBins ? Pass::GlobalU16N8 : Pass::GenericU16N8;
+  }
+  if (nb == KOHLER_N6) {
+    if (dt == KOHLER_U8) return Pass::GenericU8N6;
+    return M > kMaxSmemBins ? Pass::GlobalU16N6 : Pass::GenericU16N6;
   }
   const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
   const bool aligned16 = (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0);
@@ -212,14 +221,16 @@ KernelInfo kernel_for(Pass p, int bins, bool single) {
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16:
       return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
-    case Pass::GenericU8: return {(const void*)k_generic<1, false, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GenericU16: return {(const void*)k_generic<2, false, false>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GlobalU8: return {(const void*)k_generic<1, true, false>, kGenericWarps * 32, 0};
-    case Pass::GlobalU16: return {(const void*)k_generic<2, true, false>, kGenericWarps * 32, 0};
-    case Pass::GenericU8N8: return {(const void*)k_generic<1, false, true>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GenericU16N8: return {(const void*)k_generic<2, false, true>, kGenericWarps * 32, (size_t)bins * 4 * 4};
-    case Pass::GlobalU8N8: return {(const void*)k_generic<1, true, true>, kGenericWarps * 32, 0};
-    case Pass::GlobalU16N8: return {(const void*)k_generic<2, true, true>, kGenericWarps * 32, 0};
+    case Pass::GenericU8: return {(const void*)k_generic<1, false, 4>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16: return {(const void*)k_generic<2, false, 4>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU8: return {(const void*)k_generic<1, true, 4>, kGenericWarps * 32, 0};
+    case Pass::GlobalU16: return {(const void*)k_generic<2, true, 4>, kGenericWarps * 32, 0};
+    case Pass::GenericU8N8: return {(const void*)k_generic<1, false, 8>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16N8: return {(const void*)k_generic<2, false, 8>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU16N8: return {(const void*)k_generic<2, true, 8>, kGenericWarps * 32, 0};
+    case Pass::GenericU8N6: return {(const void*)k_generic<1, false, 6>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GenericU16N6: return {(const void*)k_generic<2, false, 6>, kGenericWarps * 32, (size_t)bins * 4 * 4};
+    case Pass::GlobalU16N6: return {(const void*)k_generic<2, true, 6>, kGenericWarps * 32, 0};
   }
   return {nullptr, 0, 0};
 }
@@ -797,8 +808,7 @@ extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t 
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   const kohler_image im{img, width, height, pitch_bytes};
   const Pass pass = pass_for(im, dt, M, nb);
-  if (pass == Pass::GlobalU8 || pass == Pass::GlobalU16 || pass == Pass::GlobalU8N8 || pass == Pass::GlobalU16N8)
-    return KOHLER_ERR_ARG;
+  if (is_global(pass)) return KOHLER_ERR_ARG;
   const int bins = bins_for(dt, M);
   char* s = static_cast<char*>(scratch);
   // the array keeps the previous call's contents: clear histograms and counters

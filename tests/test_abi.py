@@ -57,7 +57,7 @@ def test_argument_errors_without_gpu(lib_path):
     p, i64, i32, i = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
     L.kohler_curve.argtypes = [p, i, i64, i64, i64, i32, i, p, p, p, p]
     assert L.kohler_curve(None, 1, 8, 8, 8, 256, 4, None, None, None, None) == -1
-    assert L.kohler_curve(1024, 1, 8, 8, 8, 256, 6, None, None, None, None) == -2  # 6-neighbourhood: unsupported
+    assert L.kohler_curve(1024, 1, 8, 8, 8, 256, 5, None, None, None, None) == -2  # no 5-neighbourhood: unsupported
     assert L.kohler_curve(1024, 1, 8, 8, 8, 257, 4, None, None, None, None) == -1
     assert L.kohler_curve(1024, 2, 8, 8, 15, 4096, 4, None, None, None, None) == -1
     L.kohler_server_create.restype = ctypes.c_int

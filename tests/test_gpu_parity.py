@@ -228,7 +228,7 @@ def test_bad_arguments():
     assert L.kohler_curve(img.data_ptr(), 1, 8, 4, 7, 256, 4, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_ARG
     assert L.kohler_curve(img.data_ptr(), 1, 0, 4, 8, 256, 4, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_ARG
     assert L.kohler_curve(img.data_ptr(), 1, 8, 4, 8, 300, 4, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_ARG
-    assert L.kohler_curve(img.data_ptr(), 1, 8, 4, 8, 256, 6, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_UNSUPPORTED
+    assert L.kohler_curve(img.data_ptr(), 1, 8, 4, 8, 256, 5, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_UNSUPPORTED
     assert L.kohler_curve(None, 1, 8, 4, 8, 256, 4, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_ARG
     assert L.kohler_curve(img.data_ptr(), 3, 8, 4, 8, 256, 4, card.data_ptr(), card.data_ptr(), None, None) == k.ERR_ARG
 

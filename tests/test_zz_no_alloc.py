@@ -32,13 +32,13 @@ def lib():
     return K
 
 
-def regular(K, img, M):
-    card, sumc, c, ts, cnt, t0 = K.analyze_batch([img], M, MAX_K)
+def regular(K, img, M, nb=4):
+    card, sumc, c, ts, cnt, t0 = K.analyze_batch([img], M, MAX_K, nbhd=nb)
     torch.cuda.synchronize()
     return [x.cpu().numpy() for x in (card[0], sumc[0], c[0], ts[0], cnt, t0)]
 
 
-def no_alloc(K, img, M, stream):
+def no_alloc(K, img, M, stream, nb=4):
     dev = img.device
     card = torch.full((M,), -7, dtype=torch.int64, device=dev)
     sumc = torch.full((M,), -7, dtype=torch.int64, device=dev)
@@ -49,7 +49,7 @@ def no_alloc(K, img, M, stream):
     st = torch.full((1,), -7, dtype=torch.int32, device=dev)
     code = 1 if img.dtype == torch.uint8 else 2
     rc = K.lib().kohler_analyze_noalloc(img.data_ptr(), code, img.shape[1], img.shape[0],
-                                        img.stride(0) * img.element_size(), M, 4, MAX_K, card.data_ptr(),
+                                        img.stride(0) * img.element_size(), M, nb, MAX_K, card.data_ptr(),
                                         sumc.data_ptr(), c.data_ptr(), ts.data_ptr(), cnt.data_ptr(), t0.data_ptr(),
                                         st.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
     assert rc == 0, rc
@@ -77,6 +77,21 @@ def test_no_alloc_matches_regular_twice(lib, name, make, M):
         assert status == 0
         for g, w in zip(got, want):
             assert np.array_equal(g, w), f"{name}: call {call} differs"
+
+
+@pytest.mark.parametrize("nb", [8, 6])
+@pytest.mark.parametrize("name,make,M", CASES[1:], ids=[c[0] for c in CASES[1:]])
+def test_no_alloc_other_neighbourhoods(lib, name, make, M, nb):
+    K = lib
+    a = make()
+    img = torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).cuda()
+    want = regular(K, img, M, nb)
+    s = torch.cuda.Stream()
+    for call in range(2):
+        got, status = no_alloc(K, img, M, s, nb)
+        assert status == 0
+        for g, w in zip(got, want):
+            assert np.array_equal(g, w), f"{name} N{nb}: call {call} differs"
 
 
 def test_no_alloc_range_and_limits(lib):
