@@ -486,19 +486,41 @@ def form_batched(K, torch, dev, imgs_np, M, name, check_idx, peak):
                     "gpx_s_host": px / tp_host / 1e9}
     res["batched_over_plain_graph"] = tp / tb
     res["batched_over_plain_host"] = tp_host / tb_host
-    # parity of sampled images of the batch (outputs of the last plain replay
-    # and of a fresh batched call must both equal the oracle)
-    batched(torch.cuda.current_stream(dev))
-    torch.cuda.synchronize(dev)
-    ok = True
-    for j in check_idx:
-        ocard, osumc, oc, ots, ocnt, ot0 = oracle.analyze(imgs_np[j], M, MAX_K, method="alg1")
-        ok = ok and bool(np.array_equal(outs[0][j].cpu().numpy().view(np.uint64), ocard)
-                         and np.array_equal(outs[1][j].cpu().numpy().view(np.uint64), osumc)
-                         and np.array_equal(outs[2][j].cpu().numpy(), oc)
-                         and np.array_equal(outs[3][j].cpu().numpy(), ots)
-                         and int(outs[4][j]) == ocnt and int(outs[5][j]) == ot0)
-    res["parity_spot_check"] = {"images": list(check_idx), "equal": ok}
+
+    def parity():
+        # sampled images of the batch from a fresh batched call must equal the oracle
+        batched(torch.cuda.current_stream(dev))
+        torch.cuda.synchronize(dev)
+        ok = True
+        for j in check_idx:
+            ocard, osumc, oc, ots, ocnt, ot0 = oracle.analyze(imgs_np[j], M, MAX_K, method="alg1")
+            ok = ok and bool(np.array_equal(outs[0][j].cpu().numpy().view(np.uint64), ocard)
+                             and np.array_equal(outs[1][j].cpu().numpy().view(np.uint64), osumc)
+                             and np.array_equal(outs[2][j].cpu().numpy(), oc)
+                             and np.array_equal(outs[3][j].cpu().numpy(), ots)
+                             and int(outs[4][j]) == ocnt and int(outs[5][j]) == ot0)
+        return ok
+
+    res["parity_spot_check"] = {"images": list(check_idx), "equal": parity()}
+    # the autotuner's choice for this batch (every candidate checked exact by the
+    # tuner), then the same batched graph timed again with it
+    if n <= 128:
+        t0 = time.perf_counter()
+        rep = K.autotune(imgs, M, reps=5)
+        tune_s = time.perf_counter() - t0
+        gt, st = _graph_of(torch, dev, batched)
+        tt = _time_graph(torch, gt, st, reps)
+        if K.stream_status(st) != K.OK:
+            raise RuntimeError(f"{name}: tuned batched launch reported an error")
+        res["tuned"] = {"ms_graph": tt * 1e3, "gpx_s_graph": px / tt / 1e9, "hbm_frac_graph": nbytes / tt / 1e9 / peak,
+                        "over_default": tb / tt, "tune_wall_s": tune_s,
+                        "candidates": sum(len(g["candidates"]) for g in rep["groups"]),
+                        "all_candidates_exact": all(c["exact"] for g in rep["groups"] for c in g["candidates"]),
+                        "choice": [{"pass": g["pass"], "default_us": g["default_us"], **g["best"]}
+                                   for g in rep["groups"]],
+                        "parity_spot_check": parity()}
+        K.tune_clear()
+        del gt
     del imgs, outs, rows, gb, gp
     torch.cuda.empty_cache()
     return res

@@ -177,6 +177,47 @@ int kohler_release(void);
 /* Static text for a status code. */
 const char* kohler_strerror(int status);
 
+/* ---------------------------------------------------------------- autotuning
+ * Every launch over a group of images that take the same pass (the kernel the
+ * library picks from dtype, M, neighbourhood, alignment and width) has launch
+ * parameters: the route (another kernel that is also correct for all of them:
+ * the 8-byte-row uint8 pass or the general per-pair pass instead of the
+ * 16-byte-row uint8 pass, the general pass instead of the uint16 pass), the
+ * uint16 pass's block size (4, 8 or 16 warps sharing one shared-memory copy of
+ * the histograms) and pixels per lane (4 or 8), the histogram copies (blocks)
+ * per SM, and the work units per warp that size the grid.  None of them
+ * changes any result: every route computes the same exact integers.
+ *
+ * kohler_autotune times every candidate on the caller's device images (up to
+ * 128; grouped by pass as kohler_analyze_batch groups them), checks that each
+ * candidate's card and sumc equal those of the default parameters bit for bit
+ * (a candidate that differs is never chosen), and records the fastest for
+ * launches of that kind: the pass, M, and the size class floor(log2(pixels of
+ * the group)).  Later launches of any entry point (batch, curve, host path,
+ * server, allocation-free call) that match an entry use it; others use the
+ * defaults.  Each candidate is captured in a CUDA graph of `reps` launches and
+ * timed on a stream of the tuner's own that follows `cuda_stream`'s earlier
+ * work; `cuda_stream`'s later work follows the tuning runs.  The call
+ * synchronises with that work and allocates device memory (outputs for n
+ * images).  report (may be NULL): receives a NUL-terminated JSON text with
+ * every candidate's time and the choice per group, truncated to report_bytes.
+ * Errors: KOHLER_ERR_ARG (n outside 1..128, reps outside 1..1000, bad images),
+ * KOHLER_ERR_RANGE (a pixel >= M: nothing is recorded), KOHLER_ERR_CUDA. */
+int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb, int32_t reps,
+                    void* cuda_stream, char* report, int64_t report_bytes);
+
+/* The tuned entries as a JSON file at `path` (written whole), read back by
+ * kohler_tune_load, which adds the file's entries to those held (an entry for the
+ * same kind of launch is replaced).  A file that does not parse, or holds an
+ * entry that is not valid for its pass, is refused whole: KOHLER_ERR_ARG, and
+ * the table is unchanged.  Neither call touches the GPU. */
+int kohler_tune_save(const char* path);
+int kohler_tune_load(const char* path);
+/* Forgets every tuned entry (launches use the defaults again). */
+int kohler_tune_clear(void);
+/* Number of tuned entries held. */
+int32_t kohler_tune_count(void);
+
 /* ---------------------------------------------------------------- serving
  * A server turns a stream of host frames into curves and thresholds with
  * continuous batching (the video use of Section 4, Table 2): a host thread

@@ -69,6 +69,14 @@ def lib():
             if hasattr(L, "kohler_analyze_noalloc"):
                 L.kohler_analyze_noalloc.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p, p, p]
                 L.kohler_analyze_noalloc.restype = i
+            L.kohler_autotune.argtypes = [p, i32, i, i32, i, i32, p, ctypes.c_char_p, i64]
+            L.kohler_tune_save.argtypes = [ctypes.c_char_p]
+            L.kohler_tune_load.argtypes = [ctypes.c_char_p]
+            L.kohler_tune_clear.argtypes = []
+            L.kohler_tune_count.argtypes = []
+            for name in ("kohler_autotune", "kohler_tune_save", "kohler_tune_load", "kohler_tune_clear",
+                         "kohler_tune_count"):
+                getattr(L, name).restype = i
             L.kohler_release.argtypes = []
             L.kohler_strerror.argtypes = [i]
             L.kohler_strerror.restype = ctypes.c_char_p
@@ -245,6 +253,38 @@ def segment(img: torch.Tensor, M: int, thresholds: torch.Tensor, count: torch.Te
 def stream_status(stream=None) -> int:
     """Deferred status of the calls on a stream (waits for it): OK or ERR_RANGE/ERR_CUDA."""
     return lib().kohler_stream_status(_stream(stream))
+
+
+def autotune(imgs: Sequence[torch.Tensor], M: int, *, nbhd: int = KOHLER_N4, reps: int = 20, stream=None) -> dict:
+    """Times every launch configuration for these device images (up to 128), keeps
+    the fastest for later launches of the same kind, and returns the tuner's
+    report (per group of images: every candidate's time, exactness and the choice)."""
+    import json
+
+    arr, code = _images(imgs)
+    buf = ctypes.create_string_buffer(1 << 20)
+    _check(lib().kohler_autotune(arr, len(imgs), code, M, nbhd, reps, _stream(stream), buf, len(buf)),
+           "kohler_autotune")
+    return json.loads(buf.value.decode())
+
+
+def tune_save(path: str) -> None:
+    """Writes the tuned entries to a JSON file."""
+    _check(lib().kohler_tune_save(os.fsencode(path)), "kohler_tune_save")
+
+
+def tune_load(path: str) -> None:
+    """Adds the entries of a JSON file written by tune_save."""
+    _check(lib().kohler_tune_load(os.fsencode(path)), "kohler_tune_load")
+
+
+def tune_clear() -> None:
+    """Forgets every tuned entry."""
+    _check(lib().kohler_tune_clear(), "kohler_tune_clear")
+
+
+def tune_count() -> int:
+    return lib().kohler_tune_count()
 
 
 def release() -> None:

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libkohler.so")
-SOURCES = ["kohler_api.cu", "kohler_server.cu", "kohler_segment.cu"]
+SOURCES = ["kohler_api.cu", "kohler_server.cu", "kohler_segment.cu", "kohler_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

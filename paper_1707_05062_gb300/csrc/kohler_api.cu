@@ -5,10 +5,12 @@
 #include "kohler_internal.h"
 
 #include <algorithm>
+#include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <tuple>
 #include <utility>
 #include <vector>
@@ -81,6 +83,20 @@ int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int
 // `hist_words` uint64 histogram words.
 // Newly allocated memory is zeroed on the stream; a replaced workspace is freed
 // after the stream has drained.
+// Frees the workspace of `stream` once the stream's work is done, and forgets it
+// (for streams the library creates and destroys itself).
+void drop_workspace(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  cudaStreamSynchronize(stream);
+  std::lock_guard<std::mutex> lock(g_mu);
+  auto it = g_ws.find(std::make_pair(dev, (uintptr_t)stream));
+  if (it == g_ws.end()) return;
+  if (it->second->mem) cudaFree(it->second->mem);
+  delete it->second;
+  g_ws.erase(it);
+}
+
 int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_stride, Workspace** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -191,13 +207,14 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M, kohler_nbhd nb) {
   return Pass::GenericU16;
 }
 
-int strip_px(Pass p) {
+// Columns per strip of a pass (px: uint16 pixels per lane of k_fast).
+int strip_px(Pass p, int px) {
   switch (p) {
     case Pass::HistU8:
     case Pass::HistU8Check: return u8h::kStripPx;
     case Pass::FastU8:
     case Pass::FastU8Check: return u8r::kStripPx;
-    case Pass::FastU16: return 32 * TraitsU16::PX;
+    case Pass::FastU16: return 32 * px;
     default: return 32;
   }
 }
@@ -208,8 +225,21 @@ struct KernelInfo {
   size_t smem;
 };
 
+// The uint16 pass with `warps` warps per block and `px` pixels per lane.
+const void* fast_u16_fn(int warps, int px) {
+  if (px == 8) {
+    if (warps == 4) return (const void*)k_fast<TraitsU16<8>, 4, true>;
+    if (warps == 16) return (const void*)k_fast<TraitsU16<8>, 16, true>;
+    return (const void*)k_fast<TraitsU16<8>, 8, true>;
+  }
+  if (warps == 4) return (const void*)k_fast<TraitsU16<4>, 4, true>;
+  if (warps == 16) return (const void*)k_fast<TraitsU16<4>, 16, true>;
+  return (const void*)k_fast<TraitsU16<4>, 8, true>;
+}
+
 // `single`: the launch holds one image (the strip pass then takes one tensor map).
-KernelInfo kernel_for(Pass p, int bins, bool single) {
+// warps, px: the uint16 pass's block size and pixels per lane.
+KernelInfo kernel_for(Pass p, int bins, bool single, int warps = kFastWarps, int px = 4) {
   switch (p) {
     case Pass::HistU8:
       return {single ? (const void*)k_u8h<false, 1> : (const void*)k_u8h<false, kMaxBatch>, u8h::kNW * 32,
@@ -219,8 +249,7 @@ KernelInfo kernel_for(Pass p, int bins, bool single) {
               (size_t)u8h::kDynBytes};
     case Pass::FastU8: return {(const void*)k_u8r<false>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
-    case Pass::FastU16:
-      return {(const void*)k_fast<TraitsU16, kFastWarps, true>, kFastWarps * 32, (size_t)bins * 5 * 4};
+    case Pass::FastU16: return {fast_u16_fn(warps, px), warps * 32, (size_t)bins * 5 * 4};
     case Pass::GenericU8: return {(const void*)k_generic<1, false, 4>, kGenericWarps * 32, (size_t)bins * 4 * 4};
     case Pass::GenericU16: return {(const void*)k_generic<2, false, 4>, kGenericWarps * 32, (size_t)bins * 4 * 4};
     case Pass::GlobalU8: return {(const void*)k_generic<1, true, 4>, kGenericWarps * 32, 0};
@@ -279,15 +308,15 @@ Occupancy occupancy_of(const KernelInfo& k) {
 }
 
 // Grid size: enough blocks for ~units_per_warp work units per warp, at most one full
-// wave of resident blocks.
-int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp) {
+// wave of resident blocks, and at most per_sm blocks per SM (0: as many as fit).
+int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp, int per_sm = 0) {
   const Occupancy o = occupancy_of(k);
   const int64_t warps = k.threads / 32;
   int64_t want = (total_rs + warps * units_per_warp - 1) / (warps * units_per_warp);
   // one block short of a full wave: the previous launch's last block may still
   // run its epilogue on one slot when this launch starts (programmatic launch),
   // and a block waiting for that slot would finish last
-  const int64_t slots = (int64_t)o.sms * o.per_sm;
+  const int64_t slots = (int64_t)o.sms * (per_sm > 0 ? std::min(per_sm, o.per_sm) : o.per_sm);
   want = std::max<int64_t>(1, std::min<int64_t>(want, slots > 1 ? slots - 1 : 1));
   return (int)want;
 }
@@ -310,13 +339,73 @@ uint32_t completion_total(Pass p, int64_t strips, int64_t H) {
   return (uint32_t)(is_fast_u8(p) ? strips * H : strips * ((H + ur - 1) / ur));
 }
 
+// Names of the passes in tuning files and reports (in the order of Pass).
+constexpr const char* kPassNames[] = {"u8_strip",       "u8_strip_check", "u8_row",         "u8_row_check",
+                                      "u16_fast",       "u8_generic",     "u16_generic",    "u8_global",
+                                      "u16_global",     "u8_generic_n8",  "u16_generic_n8", "u16_global_n8",
+                                      "u8_generic_n6",  "u16_generic_n6", "u16_global_n6"};
+constexpr int kNumPasses = (int)(sizeof(kPassNames) / sizeof(kPassNames[0]));
+static_assert(kNumPasses == (int)Pass::GlobalU16N6 + 1, "one name per pass");
+
+// Routes that a group whose images take pass p may take instead: each one is
+// correct for every image that p accepts (its alignment, width and M rules are
+// weaker), and all fill the same histogram layout.
+bool route_ok(Pass p, Pass r) {
+  if (r == p) return true;
+  switch (p) {
+    case Pass::HistU8: return r == Pass::FastU8 || r == Pass::GenericU8;
+    case Pass::HistU8Check: return r == Pass::FastU8Check || r == Pass::GenericU8;
+    case Pass::FastU8:
+    case Pass::FastU8Check: return r == Pass::GenericU8;
+    case Pass::FastU16: return r == Pass::GenericU16;
+    default: return false;
+  }
+}
+
+// The launch parameters used when nothing is tuned.
+TuneVal default_tune(Pass p) {
+  TuneVal t;
+  t.route = (int)p;
+  t.warps = kFastWarps;
+  t.px = 4;
+  t.per_sm = 0;
+  t.upw = is_fast_u8(p) ? 2 : kRowsPerWarp;
+  return t;
+}
+
+int px_class_of(int64_t pixels) {
+  int c = 0;
+  while (c < 62 && ((int64_t)2 << c) <= pixels) ++c;
+  return c;
+}
+
 // Launches the pass over `count` images (all of one Pass) already described in
-// `idx` (indices into imgs); slots = position in the launch.
+// `idx` (indices into imgs); slots = position in the launch.  The launch
+// parameters are `force` if given, else the tuned entry for this kind of group,
+// else the defaults.
 int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* imgs, const std::vector<Band>* bands,
                  int M, int bins, Workspace* ws, LaunchParams& base, cudaStream_t stream, const std::vector<int>& slot_of,
-                 const int* out_index) {
+                 const int* out_index, const TuneVal* force = nullptr) {
   if (idx.empty()) return KOHLER_OK;
-  const int spx = strip_px(pass);
+  int64_t pixels = 0;
+  bool vec16 = true;  // every image allows 8 uint16 pixels per lane (16-byte loads)
+  for (const int i : idx) {
+    const kohler_image& im = imgs[i];
+    const int64_t rows = bands ? std::max(0, (*bands)[i].y1 - (*bands)[i].y0) : im.height;
+    pixels += im.width * rows;
+    vec16 = vec16 && (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0) && (im.width % 8 == 0);
+  }
+  TuneVal t = default_tune(pass);
+  if (force) {
+    t = *force;
+  } else {
+    TuneVal f;
+    if (tune_find(TuneKey{(int)pass, M, px_class_of(pixels)}, &f)) t = f;
+  }
+  if (!tune_valid((int)pass, t)) t = default_tune(pass);
+  if (t.px == 8 && !vec16) t.px = 4;
+  const Pass route = (Pass)t.route;
+  const int spx = strip_px(route, t.px);
   LaunchParams P = base;
   P.n = 0;
   int64_t rs = 0;
@@ -335,8 +424,8 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
     d.slot = slot_of[i];
     d.out = out_index ? out_index[i] : i;
     d.rs_begin = rs;
-    const int ur = unit_rows(pass);
-    d.units_total = completion_total(pass, d.strips, im.height);
+    const int ur = unit_rows(route);
+    d.units_total = completion_total(route, d.strips, im.height);
     rs += (int64_t)d.strips * ((d.y1 - d.y0 + ur - 1) / ur);
     ++P.n;
   }
@@ -344,10 +433,10 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   P.total_rs = rs;
   P.bins = bins;
   P.M = M;
-  KernelInfo k = kernel_for(pass, bins, P.n == 1);
+  KernelInfo k = kernel_for(route, bins, P.n == 1, t.warps, t.px);
   k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
   P.smem_bytes = (int32_t)k.smem;
-  int grid = grid_for(k, rs, is_fast_u8(pass) ? 2 : kRowsPerWarp);
+  const int grid = grid_for(k, rs, t.upw, t.per_sm);
   // programmatic dependent launch: this pass may start while the previous
   // kernel on the stream finishes (it waits for it before writing global memory)
   cudaLaunchConfig_t cfg = {};
@@ -361,14 +450,14 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if ((pass == Pass::HistU8 || pass == Pass::HistU8Check) && P.n == 1) {
+  if ((route == Pass::HistU8 || route == Pass::HistU8Check) && P.n == 1) {
     // one image: the kernel instance that takes a single tensor map
     ImgMaps<1> T1;
     const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch);
     if (rc) return rc;
     void* args[] = {&P, &T1};
     e = cudaLaunchKernelExC(&cfg, k.fn, args);
-  } else if (pass == Pass::HistU8 || pass == Pass::HistU8Check) {
+  } else if (route == Pass::HistU8 || route == Pass::HistU8Check) {
     static thread_local ImgMaps<kMaxBatch> T;  // 16 KB: kept off the stack
     for (int j = 0; j < P.n; ++j) {
       const ImgDesc& d = P.img[j];
@@ -389,7 +478,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
 int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, int32_t max_k, uint64_t* card,
               uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0,
               cudaStream_t stream, const std::vector<Band>* bands, const int* out_index = nullptr,
-              int32_t* out_status = nullptr, kohler_nbhd nb = KOHLER_N4) {
+              int32_t* out_status = nullptr, kohler_nbhd nb = KOHLER_N4, const TuneVal* force = nullptr) {
   const int bins = bins_for(dt, M);
   const int cand_stride = cand_ints(M);
   const int chunk = std::min<int>(kMaxBatch, std::max<int>(1, (int)std::min<int64_t>(
@@ -430,7 +519,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
     if (bands) sub_bands.assign(bands->begin() + c0, bands->begin() + c0 + cn);
     for (auto& g : groups) {
       rc = launch_group(g.first, g.second, imgs + c0, bands ? &sub_bands : nullptr, M, bins, ws, base, stream, slot_of,
-                        out_index ? out_index + c0 : nullptr);
+                        out_index ? out_index + c0 : nullptr, force);
       if (rc) return rc;
     }
   }
@@ -451,6 +540,23 @@ int validate_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t
 }  // namespace
 
 namespace kohler {
+const char* pass_name(int pass) { return pass >= 0 && pass < kNumPasses ? kPassNames[pass] : "?"; }
+
+int pass_from_name(const char* name) {
+  if (!name) return -1;
+  for (int p = 0; p < kNumPasses; ++p)
+    if (std::strcmp(name, kPassNames[p]) == 0) return p;
+  return -1;
+}
+
+bool tune_valid(int pass, const TuneVal& v) {
+  if (pass < 0 || pass >= kNumPasses || v.route < 0 || v.route >= kNumPasses) return false;
+  if (!route_ok((Pass)pass, (Pass)v.route)) return false;
+  if (v.warps != 4 && v.warps != 8 && v.warps != 16) return false;
+  if (v.px != 4 && v.px != 8) return false;
+  return v.per_sm >= 0 && v.per_sm <= 64 && v.upw >= 1 && v.upw <= (1 << 20);
+}
+
 int stream_sticky(cudaStream_t stream, unsigned** sticky) {
   Workspace* ws = nullptr;
   const int rc = get_workspace(stream, 1, 128, cand_ints(2), &ws);
@@ -496,6 +602,195 @@ int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, i
   if (!card || !sumc || max_k < 0 || (max_k > 0 && !out_t) || !out_count || !out_t0) return KOHLER_ERR_ARG;
   return run_batch(imgs, n, dt, M, max_k, card, sumc, curve, out_t, out_count, out_t0, (cudaStream_t)cuda_stream,
                    nullptr, nullptr, nullptr, nb);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Launch parameters the autotuner tries for a group whose images take pass p
+// (vec16: they allow 8 uint16 pixels per lane).
+std::vector<TuneVal> tune_candidates(Pass p, bool vec16) {
+  std::vector<TuneVal> out;
+  auto add = [&](Pass r, int warps, int px, int per_sm, int upw) {
+    TuneVal t;
+    t.route = (int)r;
+    t.warps = warps;
+    t.px = px;
+    t.per_sm = per_sm;
+    t.upw = upw;
+    out.push_back(t);
+  };
+  for (int r = 0; r < kNumPasses; ++r) {
+    const Pass route = (Pass)r;
+    if (!route_ok(p, route)) continue;
+    if (is_fast_u8(route)) {
+      for (int upw : {1, 2, 4, 8}) add(route, kFastWarps, 4, 0, upw);
+    } else if (route == Pass::FastU16) {
+      for (int warps : {4, 8, 16})
+        for (int px : {4, 8})
+          for (int per_sm : {0, 1})
+            for (int upw : {4, 16, 64})
+              if (px == 4 || vec16) add(route, warps, px, per_sm, upw);
+    } else {
+      for (int per_sm : {0, 1})
+        for (int upw : {4, 16, 64}) add(route, kFastWarps, 4, per_sm, upw);
+    }
+  }
+  return out;
+}
+
+void appendf(std::string& s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  s += buf;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb, int32_t reps,
+                    void* cuda_stream, char* report, int64_t report_bytes) {
+  int rc = validate_batch(imgs, n, dt, M, nb);
+  if (rc) return rc;
+  if (n < 1 || n > kMaxBatch || reps < 1 || reps > 1000 || (report && report_bytes < 1)) return KOHLER_ERR_ARG;
+  // the runs go to a stream of the tuner's own (after the caller's stream's
+  // earlier work), so that each configuration can be captured in a graph and
+  // timed without the host's launch overhead
+  cudaStream_t caller = (cudaStream_t)cuda_stream;
+  cudaStream_t stream = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return status_of(e);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  cudaEventRecord(ev0, caller);
+  cudaStreamWaitEvent(stream, ev0, 0);
+  const int max_k = 16;
+  // outputs of the tuning runs, and the reference (default-parameter) histograms
+  const size_t cm = (size_t)n * M;
+  void* dmem = nullptr;
+  const size_t bytes = cm * 8 * 3 + (size_t)n * max_k * 4 + (size_t)n * 8;
+  e = cudaMalloc(&dmem, bytes);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev0);
+    cudaEventDestroy(ev1);
+    cudaStreamDestroy(stream);
+    return status_of(e);
+  }
+  uint64_t* card = static_cast<uint64_t*>(dmem);
+  uint64_t* sumc = card + cm;
+  double* curve = reinterpret_cast<double*>(sumc + cm);
+  int32_t* out_t = reinterpret_cast<int32_t*>(curve + cm);
+  int32_t* out_count = out_t + (size_t)n * max_k;
+  int32_t* out_t0 = out_count + n;
+  std::vector<uint64_t> ref(2 * cm), got(2 * cm);
+  std::string rep = "{\"groups\": [";
+  std::map<Pass, std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) groups[pass_for(imgs[i], dt, M, nb)].push_back(i);
+  bool first_group = true;
+  for (auto& g : groups) {
+    if (rc) break;
+    const Pass pass = g.first;
+    std::vector<kohler_image> sub;
+    int64_t pixels = 0;
+    bool vec16 = true;
+    for (const int i : g.second) {
+      sub.push_back(imgs[i]);
+      pixels += imgs[i].width * imgs[i].height;
+      vec16 = vec16 && (((uintptr_t)imgs[i].img & 15) == 0) && ((imgs[i].pitch_bytes & 15) == 0) &&
+              (imgs[i].width % 8 == 0);
+    }
+    const int gn = (int)sub.size();
+    const size_t gm = (size_t)gn * M;
+    auto launch = [&](const TuneVal& t) {
+      return run_batch(sub.data(), gn, dt, M, max_k, card, sumc, curve, out_t, out_count, out_t0, stream, nullptr,
+                       nullptr, nullptr, nb, &t);
+    };
+    // One untimed run whose histograms go to `hist`, then `reps` runs captured
+    // in a graph, replayed once untimed and once timed.  Returns the mean time
+    // per launch in microseconds, or a negative value on an error.
+    auto time_one = [&](const TuneVal& t, std::vector<uint64_t>* hist) -> double {
+      if (launch(t)) return -1.0;
+      if (cudaMemcpyAsync(hist->data(), card, gm * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+          cudaMemcpyAsync(hist->data() + cm, sumc, gm * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+          cudaStreamSynchronize(stream) != cudaSuccess)
+        return -1.0;
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return -1.0;
+      int r = 0;
+      for (int k = 0; k < reps && r == 0; ++k) r = launch(t);
+      const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
+      double us = -1.0;
+      if (r == 0 && ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaGraphLaunch(exec, stream) == cudaSuccess && cudaEventRecord(ev0, stream) == cudaSuccess &&
+            cudaGraphLaunch(exec, stream) == cudaSuccess && cudaEventRecord(ev1, stream) == cudaSuccess &&
+            cudaEventSynchronize(ev1) == cudaSuccess && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess)
+          us = 1e3 * (double)ms / reps;
+      }
+      if (exec) cudaGraphExecDestroy(exec);
+      if (graph) cudaGraphDestroy(graph);
+      return us;
+    };
+    const TuneVal def = default_tune(pass);
+    const double def_us = time_one(def, &ref);
+    if (def_us < 0) {
+      rc = KOHLER_ERR_CUDA;
+      break;
+    }
+    rc = kohler_stream_status(stream);  // a pixel >= M: nothing to tune
+    if (rc) break;
+    TuneVal best = def;
+    best.us = def_us;
+    appendf(rep, "%s\n {\"pass\": \"%s\", \"M\": %d, \"px_class\": %d, \"images\": %d, \"pixels\": %lld, "
+            "\"default_us\": %.3f, \"candidates\": [", first_group ? "" : ",", pass_name((int)pass), M,
+            px_class_of(pixels), gn, (long long)pixels, def_us);
+    first_group = false;
+    bool first = true;
+    for (const TuneVal& t : tune_candidates(pass, vec16)) {
+      const double us = time_one(t, &got);
+      const bool exact = us >= 0 && std::equal(got.begin(), got.begin() + gm, ref.begin()) &&
+                         std::equal(got.begin() + cm, got.begin() + cm + gm, ref.begin() + cm);
+      appendf(rep, "%s\n  {\"route\": \"%s\", \"warps\": %d, \"px\": %d, \"per_sm\": %d, \"upw\": %d, "
+              "\"us\": %.3f, \"exact\": %s}", first ? "" : ",", pass_name(t.route), t.warps, t.px, t.per_sm, t.upw,
+              us, exact ? "true" : "false");
+      first = false;
+      if (us < 0) {
+        rc = KOHLER_ERR_CUDA;
+        break;
+      }
+      if (exact && us < best.us) {
+        best = t;
+        best.us = us;
+      }
+    }
+    appendf(rep, "],\n  \"best\": {\"route\": \"%s\", \"warps\": %d, \"px\": %d, \"per_sm\": %d, \"upw\": %d, "
+            "\"us\": %.3f}}", pass_name(best.route), best.warps, best.px, best.per_sm, best.upw, best.us);
+    if (!rc) tune_put(TuneKey{(int)pass, M, px_class_of(pixels)}, best);
+  }
+  rep += "\n]}";
+  if (!rc) rc = kohler_stream_status(stream);
+  drop_workspace(stream);
+  cudaFree(dmem);
+  // the caller's later work on its stream follows the tuning runs
+  cudaEventRecord(ev1, stream);
+  cudaStreamWaitEvent(caller, ev1, 0);
+  cudaStreamSynchronize(stream);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  cudaStreamDestroy(stream);
+  if (report) {
+    const size_t len = std::min(rep.size(), (size_t)report_bytes - 1);
+    std::memcpy(report, rep.data(), len);
+    report[len] = '\0';
+  }
+  return rc;
 }
 
 int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int32_t M, int32_t max_k,

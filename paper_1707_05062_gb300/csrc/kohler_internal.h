@@ -1,4 +1,5 @@
-// Internal interface between the C ABI translation unit and the server.
+// Internal interface between the C ABI translation unit, the server, the
+// segmentation unit and the tuning table.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -29,5 +30,32 @@ int stream_sticky(cudaStream_t stream, unsigned** sticky);
 
 // Frees the segmentation scratch of every stream of device `dev`.
 void release_segment(int dev);
+
+// ----------------------------------------------------------------- autotuning
+// Launch parameters of one group of images that take the same pass.
+struct TuneVal {
+  int route = -1;   // pass launched instead (one of the group pass's alternatives)
+  int warps = 0;    // warps per block of the uint16 pass: 4, 8 or 16 (others: fixed)
+  int px = 0;       // uint16 pixels per lane: 4 or 8
+  int per_sm = 0;   // blocks (histogram copies) per SM at most; 0: as many as fit
+  int upw = 0;      // work units per warp aimed at when sizing the grid
+  double us = 0.0;  // time per launch the tuner measured (reported, not used)
+};
+// What a tuned entry applies to: the pass the images take by default, M, and the
+// size class floor(log2(pixels of the launch group)).
+struct TuneKey {
+  int pass = -1, M = 0, px_class = 0;
+  bool operator<(const TuneKey& o) const {
+    if (pass != o.pass) return pass < o.pass;
+    if (M != o.M) return M < o.M;
+    return px_class < o.px_class;
+  }
+};
+bool tune_find(const TuneKey& k, TuneVal* v);
+void tune_put(const TuneKey& k, const TuneVal& v);
+// Pass names used in tuning files and reports, and the routes a pass may take.
+const char* pass_name(int pass);
+int pass_from_name(const char* name);  // -1 if unknown
+bool tune_valid(int pass, const TuneVal& v);
 
 }  // namespace kohler

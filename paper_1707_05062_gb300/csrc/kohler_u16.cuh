@@ -1,25 +1,35 @@
 // Device code of libkohler: the uint16 pass (k_fast).
 #pragma once
+#include <type_traits>
+
 #include "kohler_common.cuh"
 
 namespace kohler {
 
 // ----------------------------------------------------------------------------- uint16 pass traits
-// Pixels travel as pairs of 16-bit lanes in 32-bit registers.
+// Pixels travel as pairs of 16-bit lanes in 32-bit registers; a lane loads its
+// PXN pixels of a row with one 8-byte (PXN = 4) or 16-byte (PXN = 8) load.
+template <int PXN>
 struct TraitsU16 {
-  static constexpr int PX = 4;
-  static constexpr int NV = 2;
+  static_assert(PXN == 4 || PXN == 8, "4 or 8 pixels per lane");
+  static constexpr int PX = PXN;
+  static constexpr int NV = PXN / 2;
   static constexpr int ELEM = 2;
-  static __device__ __forceinline__ void unpack(uint2 raw, uint32_t (&v)[NV]) {
-    v[0] = raw.x;
-    v[1] = raw.y;
+  using Raw = typename std::conditional<PXN == 4, uint2, uint4>::type;
+  static __device__ __forceinline__ Raw zero() {
+    Raw r;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&r);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = 0u;
+    return r;
+  }
+  static __device__ __forceinline__ Raw load(const unsigned char* p) { return __ldg(reinterpret_cast<const Raw*>(p)); }
+  static __device__ __forceinline__ void unpack(const Raw& raw, uint32_t (&v)[NV]) {
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(&raw);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = w[k];
   }
 };
-
-template <int ELEM>
-__device__ __forceinline__ uint2 load8(const unsigned char* p) {
-  return __ldg(reinterpret_cast<const uint2*>(p));
-}
 
 // Flush the CTA's shared histograms of image i into its global slot and clear them.
 __device__ __forceinline__ void flush_cta(const LaunchParams& P, int i, uint32_t* hs, uint32_t* lo, uint32_t* cnt,
@@ -50,7 +60,10 @@ __device__ __forceinline__ void flush_cta(const LaunchParams& P, int i, uint32_t
 // value the shared-memory unit can merge across lanes): the pixel count at f(p),
 // and per pair its lower end (H_lo directly) and its sum s.  H_hi then follows
 // as 4 * count - border - H_lo, as in the uint8 pass.
-// Requirements (checked on the host): W % PX == 0, base and pitch multiples of 8.
+// Requirements (checked on the host): W % PX == 0, base and pitch multiples of
+// 2 PX bytes (the size of a lane's load).  NW warps of a block share one copy of
+// the histograms (the block size and the privatisation factor are the
+// autotuner's choice, with PX and the grid size).
 template <class T, int NW, bool CHECK>
 __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ LaunchParams P) {
   extern __shared__ __align__(16) uint32_t smem[];
@@ -100,17 +113,18 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
       const unsigned char* col = d.base + (int64_t)x0 * T::ELEM;
       // one row of this lane: its PX pixels, plus (lane 31) the pixel just right
       // of the strip, which the next strip's warp owns
-      auto load_row = [&](int yy, uint2& raw, uint32_t& edge) {
-        raw = make_uint2(0u, 0u);
+      using Raw = typename T::Raw;
+      auto load_row = [&](int yy, Raw& raw, uint32_t& edge) {
+        raw = T::zero();
         edge = 0u;
         if (act && yy < H) {
           const unsigned char* pr = col + (int64_t)yy * pitch;
-          raw = load8<T::ELEM>(pr);
+          raw = T::load(pr);
           if (need_right) edge = __ldg(reinterpret_cast<const uint16_t*>(pr + PX * 2));
         }
       };
       uint32_t V[NV], N[NV];
-      uint2 rc, pf0, pf1;
+      Raw rc, pf0, pf1;
       uint32_t ec, ef0, ef1;
       load_row(ya, rc, ec);
       load_row(ya + 1, pf0, ef0);
@@ -122,7 +136,7 @@ __global__ void __launch_bounds__(NW * 32) k_fast(const __grid_constant__ Launch
       }
       for (int y = ya; y < yb; ++y) {
         const bool has_down = y + 1 < H;
-        const uint2 rn = pf0;
+        const Raw rn = pf0;
         const uint32_t en = ef0;
         pf0 = pf1;
         ef0 = ef1;

@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "kohler.h")
 def declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s+(kohler_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int32_t|const char\s*\*)\s+(kohler_\w+)\s*\(", text, flags=re.M)))
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +31,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_submit", "kohler_poll",
                      "kohler_analyze_batch", "kohler_analyze_host", "kohler_server_create", "kohler_server_destroy",
-                     "kohler_strerror", "kohler_stream_status", "kohler_segment"):
+                     "kohler_strerror", "kohler_stream_status", "kohler_segment", "kohler_autotune",
+                     "kohler_tune_save", "kohler_tune_load", "kohler_tune_clear", "kohler_tune_count"):
         assert required in names
 
 

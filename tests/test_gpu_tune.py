@@ -1,0 +1,188 @@
+"""The autotuner and the launch parameters it chooses, on the GPU.
+
+No launch parameter may change a result: every route, block size, pixel count
+per lane, histogram copies per SM and grid size computes the same exact
+integers.  Each non-default kernel instance is forced through a tuning file
+and its outputs compared with the oracle element by element (tolerance 0).
+kohler_autotune itself must report every candidate exact, record its choice
+for the group, and leave later results unchanged.
+"""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+MAX_K = 16
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1707_05062_gb300 import build
+
+    build.build()
+    oracle.build()
+    yield
+
+
+@pytest.fixture(autouse=True)
+def clean_table():
+    import paper_1707_05062_gb300 as k
+
+    k.tune_clear()
+    yield
+    k.tune_clear()
+
+
+def K():
+    import paper_1707_05062_gb300 as k
+
+    return k
+
+
+def dev(img):
+    return torch.from_numpy(img.view(np.int16) if img.dtype == np.uint16 else img).cuda()
+
+
+def px_class(imgs):
+    return int(sum(im.size for im in imgs)).bit_length() - 1
+
+
+def check(imgs_np, M, nb=4, tag=""):
+    out = K().analyze_batch([dev(im) for im in imgs_np], M, MAX_K, nbhd=nb)
+    torch.cuda.synchronize()
+    assert K().stream_status() == K().OK
+    for i, im in enumerate(imgs_np):
+        want = oracle.analyze(im, M, MAX_K, nbhd=nb)
+        got = (out[0][i].cpu().numpy().view(np.uint64), out[1][i].cpu().numpy().view(np.uint64),
+               out[2][i].cpu().numpy(), out[3][i].cpu().numpy(), int(out[4][i]), int(out[5][i]))
+        for k in range(4):
+            assert np.array_equal(got[k], want[k]), f"{tag} image {i} output {k}"
+        assert got[4:] == want[4:], f"{tag} image {i} count/t0"
+
+
+def force(tmp_path, imgs, M, pass_name, **kw):
+    e = {"pass": pass_name, "M": M, "px_class": px_class(imgs), "route": pass_name, "warps": 8, "px": 4, "per_sm": 0,
+         "upw": 16, "us": 0.0}
+    e.update(kw)
+    path = tmp_path / "force.json"
+    path.write_text(json.dumps({"kohler_tune": 1, "entries": [e]}))
+    K().tune_load(str(path))
+    assert K().tune_count() == 1
+
+
+U16 = [synth.smooth_image(31, 512, 77, 4096, np.uint16, noise_sd=30.0),
+       synth.smooth_image(32, 264, 130, 4096, np.uint16, noise_sd=30.0)]
+
+
+@pytest.mark.parametrize("warps", [4, 8, 16])
+@pytest.mark.parametrize("px", [4, 8])
+@pytest.mark.parametrize("per_sm,upw", [(0, 16), (1, 4), (1, 64)])
+def test_u16_pass_instances(tmp_path, warps, px, per_sm, upw):
+    force(tmp_path, U16, 4096, "u16_fast", warps=warps, px=px, per_sm=per_sm, upw=upw)
+    check(U16, 4096, tag=f"warps={warps} px={px} per_sm={per_sm} upw={upw}")
+
+
+def test_u16_eight_pixels_falls_back_on_narrow_alignment(tmp_path):
+    # width 132: a multiple of 4, not of 8; 8 pixels per lane would not fit, so the launch takes 4
+    imgs = [synth.smooth_image(33, 132, 50, 4096, np.uint16, noise_sd=30.0)]
+    force(tmp_path, imgs, 4096, "u16_fast", warps=16, px=8, per_sm=1, upw=4)
+    check(imgs, 4096)
+
+
+def test_u16_generic_route(tmp_path):
+    force(tmp_path, U16, 4096, "u16_fast", route="u16_generic", per_sm=1, upw=64)
+    check(U16, 4096)
+
+
+U8 = [synth.voronoi_image(5, 1024, 300, 40, 4.0), synth.smooth_image(6, 528, 97, 256)]
+
+
+@pytest.mark.parametrize("route,upw", [("u8_strip", 1), ("u8_strip", 8), ("u8_row", 1), ("u8_row", 4),
+                                       ("u8_generic", 64)])
+def test_u8_routes(tmp_path, route, upw):
+    force(tmp_path, U8, 256, "u8_strip", route=route, upw=upw, per_sm=1 if route == "u8_generic" else 0)
+    check(U8, 256, tag=route)
+
+
+def test_u8_check_routes(tmp_path):
+    imgs = [synth.smooth_image(7, 528, 61, 200)]
+    for route in ("u8_row_check", "u8_generic"):
+        force(tmp_path, imgs, 200, "u8_strip_check", route=route, upw=2)
+        check(imgs, 200, tag=route)
+        K().tune_clear()
+
+
+def test_other_size_class_is_not_affected(tmp_path):
+    force(tmp_path, U8, 256, "u8_strip", route="u8_generic", upw=64)
+    small = [synth.smooth_image(8, 64, 16, 256)]  # another size class: the defaults
+    check(small, 256)
+
+
+@pytest.mark.parametrize("nb", [8, 6])
+def test_neighbourhood_grid_parameters(tmp_path, nb):
+    imgs = [synth.smooth_image(9, 300, 211, 256)]
+    force(tmp_path, imgs, 256, f"u8_generic_n{nb}", per_sm=1, upw=4)
+    check(imgs, 256, nb=nb)
+
+
+def test_autotune_u16_and_u8_batch():
+    k = K()
+    imgs = U8 + [synth.smooth_image(10, 77, 45, 256)]  # two groups: the strip pass and the general pass
+    rep = k.autotune([dev(im) for im in imgs], 256, reps=3)
+    names = sorted(g["pass"] for g in rep["groups"])
+    assert names == ["u8_generic", "u8_strip"]
+    for g in rep["groups"]:
+        assert g["candidates"] and all(c["exact"] for c in g["candidates"])
+        assert g["best"]["us"] <= g["default_us"] + 1e-9
+        assert g["best"]["us"] == min([g["default_us"]] + [c["us"] for c in g["candidates"]])
+    assert k.tune_count() == 2
+    check(imgs, 256, tag="after tuning")
+    rep16 = k.autotune([dev(im) for im in U16], 4096, reps=3)
+    (g,) = rep16["groups"]
+    assert g["pass"] == "u16_fast" and g["px_class"] == px_class(U16)
+    assert {(c["warps"], c["px"]) for c in g["candidates"] if c["route"] == "u16_fast"} == {
+        (w, p) for w in (4, 8, 16) for p in (4, 8)}
+    assert all(c["exact"] for c in g["candidates"])
+    check(U16, 4096, tag="after tuning")
+
+
+def test_autotune_refuses_out_of_range_pixels():
+    k = K()
+    img = synth.smooth_image(11, 64, 32, 100)
+    img[3, 5] = 120
+    with pytest.raises(k.KohlerError) as e:
+        k.autotune([dev(img)], 100, reps=2)
+    assert e.value.status == k.ERR_RANGE
+    assert k.tune_count() == 0
+
+
+def test_autotune_arguments():
+    k = K()
+    img = dev(synth.smooth_image(12, 64, 32, 256))
+    for reps in (0, 1001):
+        with pytest.raises(k.KohlerError):
+            k.autotune([img], 256, reps=reps)
+    with pytest.raises(k.KohlerError):
+        k.autotune([img] * 129, 256, reps=1)
+
+
+def test_tuned_graph_capture_and_stream_order():
+    # tuning on a side stream follows that stream's earlier work and precedes its later work
+    k = K()
+    s = torch.cuda.Stream()
+    src = synth.voronoi_image(13, 2048, 512, 60, 4.0)
+    with torch.cuda.stream(s):
+        img = torch.empty((512, 2048), dtype=torch.uint8, device="cuda")
+        img.copy_(torch.from_numpy(src).cuda(non_blocking=True))
+        k.autotune([img], 256, reps=2, stream=s)
+        out = k.analyze_batch([img], 256, MAX_K, stream=s)
+    s.synchronize()
+    want = oracle.analyze(src, 256, MAX_K)
+    assert np.array_equal(out[0][0].cpu().numpy().view(np.uint64), want[0])
