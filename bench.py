@@ -908,6 +908,51 @@ def bench_reference(args, rank, world):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# Small fixed workloads for ncu captures of one kernel: a few untimed launches,
+# then `launches` launches of the case, nothing else on the GPU.
+NCU_CASES = ("u16_batch16", "u16_batch16_tuned", "n8_18mp", "n6_18mp", "segment_18mp")
+
+
+def ncu_case(name: str, launches: int = 3) -> int:
+    import tempfile
+
+    import torch
+
+    import paper_1707_05062_gb300 as K
+    import synth
+    from paper_1707_05062_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    if name.startswith("u16_batch16"):
+        imgs_np = synth.cosine_u16_batch()
+        imgs = [torch.from_numpy(im.view(np.int16)).to(dev) for im in imgs_np]
+        M = 4096
+        if name.endswith("_tuned"):
+            # the autotuner's choice for this batch: 16 warps, 8 pixels per lane, 64 rows per warp
+            px = sum(im.size for im in imgs_np)
+            entry = {"pass": "u16_fast", "M": M, "px_class": int(px).bit_length() - 1, "route": "u16_fast",
+                     "warps": 16, "px": 8, "per_sm": 0, "upw": 64, "us": 0.0}
+            with tempfile.NamedTemporaryFile("w", suffix=".json", delete=False) as f:
+                json.dump({"kohler_tune": 1, "entries": [entry]}, f)
+            K.tune_load(f.name)
+            os.unlink(f.name)
+        run = lambda: K.analyze_batch(imgs, M, MAX_K)
+    else:
+        img = torch.from_numpy(synth.voronoi_18mp()).to(dev)
+        if name == "segment_18mp":
+            res = K.analyze_batch([img], 256, 6)
+            out = torch.empty_like(img)
+            run = lambda: K.segment(img, 256, res[3][0], res[4][0], out=out)
+        else:
+            nb = 8 if name == "n8_18mp" else 6
+            run = lambda: K.analyze_batch([img], 256, MAX_K, nbhd=nb)
+    for _ in range(2 + launches):
+        run()
+    torch.cuda.synchronize(dev)
+    return 0 if K.stream_status() == K.OK else 1
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -921,7 +966,11 @@ def main(argv=None):
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served,segment,nbhd",
                     help="comma list of extra forms reported in the same line (N = 1 only); empty for none")
+    ap.add_argument("--ncu-case", choices=NCU_CASES, default=None,
+                    help="run only a small fixed workload of one kernel (for ncu captures) and exit")
     args = ap.parse_args(argv)
+    if args.ncu_case:
+        return ncu_case(args.ncu_case)
     if args.warmup < 3:
         args.warmup = 3
     rank, local, world = dist_env()

@@ -165,9 +165,10 @@ __device__ __forceinline__ void block_excl_scan_n(uint64_t (&v)[N], uint64_t* sc
 }
 
 // ----------------------------------------------------------------------------- epilogue
-template <bool GLOBAL>
-__device__ __forceinline__ uint64_t ldh(const unsigned long long* p) {
-  return GLOBAL ? __ldcg(p) : *p;
+template <bool GLOBAL, class HT>
+__device__ __forceinline__ uint64_t ldh(const HT* p) {
+  if constexpr (GLOBAL) return __ldcg(p);
+  else return (uint64_t)*p;
 }
 
 // Curve of one image from its three histograms (one block, blockDim.x threads).
@@ -175,12 +176,12 @@ __device__ __forceinline__ uint64_t ldh(const unsigned long long* p) {
 // sumc(t)  = RLH(t) - RS(t),  RLH(t) = sum_{u < t} (cumL(u) + cumH(u)),
 //            RS(t) = sum_{1 <= u <= t} (2 cumS(2u - 2) + H_s(2u - 1))
 // where cumX are inclusive prefix sums.  H_GLOBAL: histograms in global memory
-// (read through L2), else in shared memory.  Writes card and sumc to both
-// (card_o, sumc_o: global outputs; card_s, sumc_s: optional shared copies) and
-// curve (if non-null).  When `bad` the outputs are all zero.  One block.
-template <bool H_GLOBAL>
-__device__ void curve_epilogue(const unsigned long long* hlo, const unsigned long long* hhi,
-                               const unsigned long long* hs, int M, bool bad, uint64_t* __restrict__ card_o,
+// (read through L2), else in shared memory, as uint64 or (HT = uint32_t) as
+// uint32.  Writes card and sumc to both (card_o, sumc_o: global outputs;
+// card_s, sumc_s: optional shared copies) and curve (if non-null).  When `bad`
+// the outputs are all zero.  One block.
+template <bool H_GLOBAL, class HT = unsigned long long>
+__device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M, bool bad, uint64_t* __restrict__ card_o,
                                uint64_t* __restrict__ sumc_o, double* __restrict__ curve, uint64_t* card_s,
                                uint64_t* sumc_s, uint64_t* scratch) {
   const int nt = blockDim.x;
@@ -192,11 +193,11 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
   uint64_t sl = 0, sh = 0, ss = 0;
 #pragma unroll 8
   for (int t = c0; t < c1; ++t) {
-    sl += ldh<H_GLOBAL>(hlo + t);
-    sh += ldh<H_GLOBAL>(hhi + t);
+    sl += ldh<H_GLOBAL, HT>(hlo + t);
+    sh += ldh<H_GLOBAL, HT>(hhi + t);
   }
 #pragma unroll 8
-  for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL>(hs + u);
+  for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL, HT>(hs + u);
   uint64_t v3[3] = {sl, sh, ss};
   block_excl_scan_n<3>(v3, scratch);
   const uint64_t baseL = v3[0], baseH = v3[1];
@@ -206,19 +207,19 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
   {
     uint64_t cl = baseL, ch = baseH;
     // cumS_excl(u) = sum_{v < u} H_s(v); start at u = 2 c0 - 1
-    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + 2 * c0 - 1) : 0;
     uint64_t cs_excl = baseS - hprev;  // cumS_excl(2 c0 - 1)
 #pragma unroll 8
     for (int t = c0; t < c1; ++t) {
-      cl += ldh<H_GLOBAL>(hlo + t);
-      ch += ldh<H_GLOBAL>(hhi + t);
+      cl += ldh<H_GLOBAL, HT>(hlo + t);
+      ch += ldh<H_GLOBAL, HT>(hhi + t);
       sa += cl + ch;
       if (t > 0) {
-        const uint64_t h1 = ldh<H_GLOBAL>(hs + 2 * t - 1);
+        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + 2 * t - 1);
         sg += 2 * cs_excl + h1;  // 2 cumS(2t - 2) + H_s(2t - 1)
-        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL>(hs + 2 * t) : 0);  // -> cumS_excl(2t + 1)
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + 2 * t) : 0);  // -> cumS_excl(2t + 1)
       } else {
-        cs_excl += (S > 0 ? ldh<H_GLOBAL>(hs + 0) : 0);  // cumS_excl(1)
+        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs + 0) : 0);  // cumS_excl(1)
       }
     }
   }
@@ -229,18 +230,18 @@ __device__ void curve_epilogue(const unsigned long long* hlo, const unsigned lon
   // pass 3: outputs
   {
     uint64_t cl = baseL, ch = baseH, rlh = baseA, rs = baseG;
-    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL>(hs + 2 * c0 - 1) : 0;
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + 2 * c0 - 1) : 0;
     uint64_t cs_excl = baseS - hprev;
 #pragma unroll 8
     for (int t = c0; t < c1; ++t) {
-      cl += ldh<H_GLOBAL>(hlo + t);
-      ch += ldh<H_GLOBAL>(hhi + t);
+      cl += ldh<H_GLOBAL, HT>(hlo + t);
+      ch += ldh<H_GLOBAL, HT>(hhi + t);
       if (t > 0) {
-        const uint64_t h1 = ldh<H_GLOBAL>(hs + 2 * t - 1);
+        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + 2 * t - 1);
         rs += 2 * cs_excl + h1;
-        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL>(hs + 2 * t) : 0);
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + 2 * t) : 0);
       } else {
-        cs_excl += (S > 0 ? ldh<H_GLOBAL>(hs + 0) : 0);
+        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs + 0) : 0);
       }
       const uint64_t k = bad ? 0 : cl - ch;
       const uint64_t sm = bad ? 0 : rlh - rs;
@@ -299,13 +300,48 @@ __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, in
   float* const cf = reinterpret_cast<float*>(cand + cand_ints(M) / 2);
   if (tid == 0) sh_int[0] = 0;
   __syncthreads();
-  // 1. plateau starts that are local maxima (in no particular order)
-  for (int t = tid; t < M; t += nt)
-    if (is_max_start(card, sumc, M, t)) {
-      const int k = atomicAdd(&sh_int[0], 1);
+  // 1. plateau starts that are local maxima (in no particular order).  A warp
+  //    takes 32 consecutive t; lane l finds whether C(t) is valid and the sign
+  //    of C(t + 1) - C(t) (one exact comparison), and ballots follow each
+  //    plateau to its end inside the warp (past it: is_max_start).  The warp
+  //    reserves its candidate slots with one shared atomic.
+  for (int w0 = warp * 32; w0 < M; w0 += nt) {
+    const int t = w0 + lane;
+    const bool valid = t < M && card[t] > 0;
+    const bool vnext = t + 1 < M && card[t + 1] > 0;
+    const int rel = (valid && vnext) ? cmp_ratio(sumc[t + 1], card[t + 1], sumc[t], card[t]) : 0;
+    bool vprev = __shfl_up_sync(0xffffffffu, valid, 1);
+    int rel_prev = __shfl_up_sync(0xffffffffu, rel, 1);  // sign of C(t) - C(t - 1)
+    if (lane == 0) {
+      vprev = t > 0 && t < M && card[t - 1] > 0;
+      rel_prev = (vprev && valid) ? cmp_ratio(sumc[t], card[t], sumc[t - 1], card[t - 1]) : 0;
+    }
+    // t starts a plateau that C rises into (or that follows an invalid t)
+    const bool left = valid && (!vprev || rel_prev > 0);
+    // the plateau of t runs while C(b + 1) = C(b); it is a maximum when the t
+    // after its end is invalid or lower
+    const unsigned eq = __ballot_sync(0xffffffffu, valid && vnext && rel == 0);
+    const unsigned down = __ballot_sync(0xffffffffu, !vnext || rel < 0);
+    bool m = false;
+    if (left) {
+      const unsigned rest = ~eq >> lane;  // bit k: the plateau ends at lane + k
+      if (rest != 0u) {
+        const int b = lane + __ffs(rest) - 1;
+        m = ((down >> b) & 1u) != 0u;
+      } else {
+        m = is_max_start(card, sumc, M, t);  // the plateau goes on past this warp's values
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(&sh_int[0], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (m) {
+      const int k = base + __popc(bal & ((1u << lane) - 1u));
       cand[k] = t;
       cf[k] = (float)sumc[t] / (float)card[t];
     }
+  }
   __syncthreads();
   const int K = sh_int[0];
   const int need = max_k > 1 ? max_k : 1;  // ranks that matter: below max_k, and rank 0 (t0)
@@ -323,9 +359,17 @@ __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, in
     for (int shift = 24; shift >= 0; shift -= 8) {
       for (int b = tid; b < 256; b += nt) hist[b] = 0u;
       __syncthreads();
-      for (int i = tid; i < K; i += nt) {
-        const uint32_t u = __float_as_uint(cf[i]);
-        if ((u & pmask) == prefix) atomicAdd(&hist[(u >> shift) & 255u], 1u);
+      // near-equal C values share digits: lanes with the same digit add once
+      for (int w0 = warp * 32; w0 < K; w0 += nt) {
+        const int i = w0 + lane;
+        const uint32_t u = i < K ? __float_as_uint(cf[i]) : 0u;
+        const bool in = i < K && (u & pmask) == prefix;
+        const uint32_t digit = (u >> shift) & 255u;
+        const unsigned act = __ballot_sync(0xffffffffu, in);
+        if (in) {
+          const unsigned peers = __match_any_sync(act, digit);
+          if (lane == __ffs(peers) - 1) atomicAdd(&hist[digit], (unsigned)__popc(peers));
+        }
       }
       __syncthreads();
       if (warp == 0) {
@@ -361,17 +405,43 @@ __device__ void select_thresholds(const uint64_t* card, const uint64_t* sumc, in
     }
     cut = __uint_as_float(prefix) * 0.999996185302734375f;  // x (1 - 2^-18), below x (1 - 2^-19)
   }
-  // 3. rank of a remaining candidate = number of candidates before it: one warp
-  //    per candidate, one comparison per lane and batch of 32; counting stops
-  //    once the rank reaches `need`
-  for (int i = warp; i < K; i += nw) {
+  // 3. the candidates at or above the cut, gathered into a short list `sel`.
+  //    A candidate whose rank is below `need` has a float C of at least
+  //    x (1 - 2^-19); every candidate before it then has a float C above the
+  //    cut, so its rank counted within the list is exact.  (Candidates nearer
+  //    the cut than that have at least `need` list members before them, and
+  //    are not reported.)  Rank = number of list members before it: one warp
+  //    per candidate, one comparison per lane and batch of 32, counting stops
+  //    once the rank reaches `need`.  A list longer than its space (many exact
+  //    ties) is ranked against all candidates instead.
+  constexpr int kSelCap = kShInts - 40 - 256 - 8;
+  int* const sel = sh_int + 40 + 256 + 8;
+  if (tid == 0) sh_int[3] = 0;
+  __syncthreads();
+  for (int w0 = warp * 32; w0 < K; w0 += nt) {
+    const int i = w0 + lane;
+    const bool keep = i < K && cf[i] >= cut;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    int base = 0;
+    if (lane == 0 && bal) base = atomicAdd(&sh_int[3], __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const int k = base + __popc(bal & ((1u << lane) - 1u));
+    if (keep && k < kSelCap) sel[k] = i;
+  }
+  __syncthreads();
+  const int S = sh_int[3];
+  const bool listed = S <= kSelCap;
+  const int n_rank = listed ? S : K;  // candidates ranked, and compared against
+  for (int q = warp; q < n_rank; q += nw) {
+    const int i = listed ? sel[q] : q;
     const float fi = cf[i];
     if (fi < cut) continue;
     const int ti = cand[i];
     int before = 0;
-    for (int base = 0; base < K && before < need; base += 32) {
-      const int j = base + lane;
-      const bool b = j < K && j != i && ranks_before(card, sumc, cand[j], cf[j], ti, fi);
+    for (int base = 0; base < n_rank && before < need; base += 32) {
+      const int r = base + lane;
+      const int j = r < n_rank ? (listed ? sel[r] : r) : -1;
+      const bool b = j >= 0 && j != i && ranks_before(card, sumc, cand[j], cf[j], ti, fi);
       before += __popc(__ballot_sync(0xffffffffu, b));
     }
     if (lane == 0) {
@@ -408,6 +478,9 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   const size_t need_h = (size_t)4 * bins * 8;
   const bool stage_cs = dsm_bytes >= need_cs + need_cand;
   const bool stage_h = dsm_bytes >= need_cs + need_cand + need_h;
+  // else the histograms as uint32, when every count fits: each counts pairs,
+  // at most 4 per pixel (N8), so images below 2^30 pixels qualify
+  const bool stage_h32 = !stage_h && stage_cs && dsm_bytes >= need_h / 2 && (int64_t)d.W * d.H < ((int64_t)1 << 30);
   uint64_t* card_s = stage_cs ? reinterpret_cast<uint64_t*>(dsm) : nullptr;
   uint64_t* sumc_s = stage_cs ? card_s + M : nullptr;
   int32_t* cand = stage_cs ? reinterpret_cast<int32_t*>(dsm + need_cs) : P.cand + (size_t)d.slot * P.cand_stride;
@@ -422,6 +495,53 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
     if (P.out_count)
       select_thresholds(card_s, sumc_s, M, P.max_k, P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr,
                         P.out_count + d.out, P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
+  } else if (stage_h32) {
+    // histograms as uint32 in shared memory for the scans; card and sumc go
+    // to global memory only, then come back into the same shared memory for
+    // the threshold search
+    uint32_t* h32 = reinterpret_cast<uint32_t*>(dsm);
+    for (int b0 = threadIdx.x; b0 < 4 * bins; b0 += 8 * blockDim.x) {
+      uint64_t v8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + u * blockDim.x;
+        v8[u] = b < 4 * bins ? __ldcg(h + b) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int b = b0 + u * blockDim.x;
+        if (b < 4 * bins) {
+          h32[b] = (uint32_t)v8[u];
+          h[b] = 0ull;
+        }
+      }
+    }
+    __syncthreads();
+    curve_epilogue<false, uint32_t>(h32, h32 + bins, h32 + 2 * bins, M, bad, card, sumc, curve, nullptr, nullptr,
+                                    scratch);
+    if (P.out_count) {
+      // eight rows of loads in flight per thread
+      for (int t0 = threadIdx.x; t0 < M; t0 += 8 * blockDim.x) {
+        uint64_t c8[8], s8[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * blockDim.x;
+          c8[u] = t < M ? __ldcg(reinterpret_cast<const unsigned long long*>(card) + t) : 0ull;
+          s8[u] = t < M ? __ldcg(reinterpret_cast<const unsigned long long*>(sumc) + t) : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int t = t0 + u * blockDim.x;
+          if (t < M) {
+            card_s[t] = c8[u];
+            sumc_s[t] = s8[u];
+          }
+        }
+      }
+      __syncthreads();
+      select_thresholds(card_s, sumc_s, M, P.max_k, P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr,
+                        P.out_count + d.out, P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
+    }
   } else {
     curve_epilogue<true>(h, h + bins, h + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
     for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) h[b] = 0ull;

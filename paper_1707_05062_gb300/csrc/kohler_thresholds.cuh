@@ -30,9 +30,22 @@ __global__ void __launch_bounds__(kEpiThreads) k_thresholds(const __grid_constan
   if (Q.staged) {
     uint64_t* c = reinterpret_cast<uint64_t*>(dsm);
     uint64_t* s = c + Q.M;
-    for (int t = threadIdx.x; t < Q.M; t += blockDim.x) {
-      c[t] = card[t];
-      s[t] = sumc[t];
+    for (int t0 = threadIdx.x; t0 < Q.M; t0 += 8 * blockDim.x) {  // eight loads in flight per array
+      uint64_t c8[8], s8[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        c8[u] = t < Q.M ? card[t] : 0ull;
+        s8[u] = t < Q.M ? sumc[t] : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int t = t0 + u * blockDim.x;
+        if (t < Q.M) {
+          c[t] = c8[u];
+          s[t] = s8[u];
+        }
+      }
     }
     card = c;
     sumc = s;
