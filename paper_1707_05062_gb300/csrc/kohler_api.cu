@@ -269,7 +269,8 @@ KernelInfo kernel_for(Pass p, int bins, bool single, int warps = kFastWarps, int
 // below 100 KB (the block's own pass needs `pass_smem`).
 size_t epilogue_smem(int M, int bins, size_t pass_smem) {
   const size_t cs = (size_t)2 * M * 8 + ((size_t)cand_ints(M) * 4 + 15) / 16 * 16;
-  const size_t full = cs + (size_t)4 * bins * 8;
+  // + the three histograms as uint64 with one pad slot per 16 (see finish_image)
+  const size_t full = cs + (size_t)(2 * (bins + bins / 16 + 1) + (2 * bins + 2 * bins / 16 + 1)) * 8;
   const size_t cap = 100 * 1024;
   if (full <= cap) return full;
   if (cs <= cap || cs <= pass_smem) return cs;

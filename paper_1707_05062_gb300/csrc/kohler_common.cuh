@@ -177,10 +177,20 @@ __device__ __forceinline__ uint64_t ldh(const HT* p) {
 //            RS(t) = sum_{1 <= u <= t} (2 cumS(2u - 2) + H_s(2u - 1))
 // where cumX are inclusive prefix sums.  H_GLOBAL: histograms in global memory
 // (read through L2), else in shared memory, as uint64 or (HT = uint32_t) as
-// uint32.  Writes card and sumc to both (card_o, sumc_o: global outputs;
-// card_s, sumc_s: optional shared copies) and curve (if non-null).  When `bad`
-// the outputs are all zero.  One block.
-template <bool H_GLOBAL, class HT = unsigned long long>
+// uint32.  PAD > 0: element i of each shared array sits at i + i / PAD (one pad
+// slot per 32 banks), so that threads reading consecutive chunks of the same
+// length hit distinct banks.  Writes card and sumc to both (card_o, sumc_o:
+// global outputs; card_s, sumc_s: optional shared copies) and curve (if
+// non-null).  When `bad` the outputs are all zero.  One block.
+template <int PAD>
+__device__ __forceinline__ int pad_index(int i) {
+  return PAD > 0 ? i + i / PAD : i;
+}
+template <int PAD>
+__device__ __forceinline__ int padded_len(int n) {
+  return PAD > 0 ? n + n / PAD + 1 : n;
+}
+template <bool H_GLOBAL, class HT = unsigned long long, int PAD = 0>
 __device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M, bool bad, uint64_t* __restrict__ card_o,
                                uint64_t* __restrict__ sumc_o, double* __restrict__ curve, uint64_t* card_s,
                                uint64_t* sumc_s, uint64_t* scratch) {
@@ -193,11 +203,11 @@ __device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M
   uint64_t sl = 0, sh = 0, ss = 0;
 #pragma unroll 8
   for (int t = c0; t < c1; ++t) {
-    sl += ldh<H_GLOBAL, HT>(hlo + t);
-    sh += ldh<H_GLOBAL, HT>(hhi + t);
+    sl += ldh<H_GLOBAL, HT>(hlo + pad_index<PAD>(t));
+    sh += ldh<H_GLOBAL, HT>(hhi + pad_index<PAD>(t));
   }
 #pragma unroll 8
-  for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL, HT>(hs + u);
+  for (int u = 2 * c0; u < min(2 * c1, S); ++u) ss += ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(u));
   uint64_t v3[3] = {sl, sh, ss};
   block_excl_scan_n<3>(v3, scratch);
   const uint64_t baseL = v3[0], baseH = v3[1];
@@ -207,19 +217,19 @@ __device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M
   {
     uint64_t cl = baseL, ch = baseH;
     // cumS_excl(u) = sum_{v < u} H_s(v); start at u = 2 c0 - 1
-    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + 2 * c0 - 1) : 0;
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * c0 - 1)) : 0;
     uint64_t cs_excl = baseS - hprev;  // cumS_excl(2 c0 - 1)
 #pragma unroll 8
     for (int t = c0; t < c1; ++t) {
-      cl += ldh<H_GLOBAL, HT>(hlo + t);
-      ch += ldh<H_GLOBAL, HT>(hhi + t);
+      cl += ldh<H_GLOBAL, HT>(hlo + pad_index<PAD>(t));
+      ch += ldh<H_GLOBAL, HT>(hhi + pad_index<PAD>(t));
       sa += cl + ch;
       if (t > 0) {
-        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + 2 * t - 1);
+        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * t - 1));
         sg += 2 * cs_excl + h1;  // 2 cumS(2t - 2) + H_s(2t - 1)
-        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + 2 * t) : 0);  // -> cumS_excl(2t + 1)
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * t)) : 0);  // -> cumS_excl(2t + 1)
       } else {
-        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs + 0) : 0);  // cumS_excl(1)
+        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs) : 0);  // cumS_excl(1)
       }
     }
   }
@@ -230,18 +240,18 @@ __device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M
   // pass 3: outputs
   {
     uint64_t cl = baseL, ch = baseH, rlh = baseA, rs = baseG;
-    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + 2 * c0 - 1) : 0;
+    const uint64_t hprev = (c0 > 0 && c0 < c1) ? ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * c0 - 1)) : 0;
     uint64_t cs_excl = baseS - hprev;
 #pragma unroll 8
     for (int t = c0; t < c1; ++t) {
-      cl += ldh<H_GLOBAL, HT>(hlo + t);
-      ch += ldh<H_GLOBAL, HT>(hhi + t);
+      cl += ldh<H_GLOBAL, HT>(hlo + pad_index<PAD>(t));
+      ch += ldh<H_GLOBAL, HT>(hhi + pad_index<PAD>(t));
       if (t > 0) {
-        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + 2 * t - 1);
+        const uint64_t h1 = ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * t - 1));
         rs += 2 * cs_excl + h1;
-        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + 2 * t) : 0);
+        cs_excl += h1 + (2 * t < S ? ldh<H_GLOBAL, HT>(hs + pad_index<PAD>(2 * t)) : 0);
       } else {
-        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs + 0) : 0);
+        cs_excl += (S > 0 ? ldh<H_GLOBAL, HT>(hs) : 0);
       }
       const uint64_t k = bad ? 0 : cl - ch;
       const uint64_t sm = bad ? 0 : rlh - rs;
@@ -475,23 +485,36 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   uint64_t* sumc = P.sumc + (size_t)d.out * M;
   double* curve = P.curve ? P.curve + (size_t)d.out * M : nullptr;
   const size_t need_cs = (size_t)2 * M * 8, need_cand = (size_t)cand_ints(M) * 4;
-  const size_t need_h = (size_t)4 * bins * 8;
+  // staged histograms: H_lo, H_hi (bins each) and H_s (2 bins), each padded
+  constexpr int kPad64 = 16, kPad32 = 32;
+  const int lb64 = padded_len<kPad64>(bins), sb64 = padded_len<kPad64>(2 * bins);
+  const int lb32 = padded_len<kPad32>(bins), sb32 = padded_len<kPad32>(2 * bins);
+  const size_t need_h = (size_t)(2 * lb64 + sb64) * 8;
+  const size_t need_h32 = (size_t)(2 * lb32 + sb32) * 4;
   const bool stage_cs = dsm_bytes >= need_cs + need_cand;
-  const bool stage_h = dsm_bytes >= need_cs + need_cand + need_h;
+  const size_t at_h = (need_cs + need_cand + 15) & ~(size_t)15;  // staged uint64 histograms start here
+  const bool stage_h = dsm_bytes >= at_h + need_h;
   // else the histograms as uint32, when every count fits: each counts pairs,
   // at most 4 per pixel (N8), so images below 2^30 pixels qualify
-  const bool stage_h32 = !stage_h && stage_cs && dsm_bytes >= need_h / 2 && (int64_t)d.W * d.H < ((int64_t)1 << 30);
+  const bool stage_h32 = !stage_h && stage_cs && dsm_bytes >= need_h32 && (int64_t)d.W * d.H < ((int64_t)1 << 30);
+  // destination of workspace word b (H_lo, H_hi, H_s in a row) in a padded copy
+  auto staged_at = [&](int b, int lb, auto pad_of) -> int {
+    if (b < bins) return pad_of(b);
+    if (b < 2 * bins) return lb + pad_of(b - bins);
+    return 2 * lb + pad_of(b - 2 * bins);
+  };
   uint64_t* card_s = stage_cs ? reinterpret_cast<uint64_t*>(dsm) : nullptr;
   uint64_t* sumc_s = stage_cs ? card_s + M : nullptr;
   int32_t* cand = stage_cs ? reinterpret_cast<int32_t*>(dsm + need_cs) : P.cand + (size_t)d.slot * P.cand_stride;
   if (stage_h) {
-    unsigned long long* hsm = reinterpret_cast<unsigned long long*>(dsm + ((need_cs + need_cand + 15) & ~(size_t)15));
+    unsigned long long* hsm = reinterpret_cast<unsigned long long*>(dsm + at_h);
     for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) {
-      hsm[b] = __ldcg(h + b);
+      hsm[staged_at(b, lb64, [](int i) { return pad_index<kPad64>(i); })] = __ldcg(h + b);
       h[b] = 0ull;  // clean the workspace slot for the next use
     }
     __syncthreads();
-    curve_epilogue<false>(hsm, hsm + bins, hsm + 2 * bins, M, bad, card, sumc, curve, card_s, sumc_s, scratch);
+    curve_epilogue<false, unsigned long long, kPad64>(hsm, hsm + lb64, hsm + 2 * lb64, M, bad, card, sumc, curve, card_s,
+                                                      sumc_s, scratch);
     if (P.out_count)
       select_thresholds(card_s, sumc_s, M, P.max_k, P.out_t ? P.out_t + (size_t)d.out * P.max_k : nullptr,
                         P.out_count + d.out, P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
@@ -511,14 +534,14 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
       for (int u = 0; u < 8; ++u) {
         const int b = b0 + u * blockDim.x;
         if (b < 4 * bins) {
-          h32[b] = (uint32_t)v8[u];
+          h32[staged_at(b, lb32, [](int i) { return pad_index<kPad32>(i); })] = (uint32_t)v8[u];
           h[b] = 0ull;
         }
       }
     }
     __syncthreads();
-    curve_epilogue<false, uint32_t>(h32, h32 + bins, h32 + 2 * bins, M, bad, card, sumc, curve, nullptr, nullptr,
-                                    scratch);
+    curve_epilogue<false, uint32_t, kPad32>(h32, h32 + lb32, h32 + 2 * lb32, M, bad, card, sumc, curve, nullptr, nullptr,
+                                            scratch);
     if (P.out_count) {
       // eight rows of loads in flight per thread
       for (int t0 = threadIdx.x; t0 < M; t0 += 8 * blockDim.x) {
