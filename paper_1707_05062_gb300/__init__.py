@@ -197,9 +197,11 @@ def analyze_batch(imgs: Sequence[torch.Tensor], M: int, max_k: int, *, with_curv
     return card, sumc, c, out_t[:, :max_k], cnt, t0
 
 
-def analyze_host(img, M: int, max_k: int, nbhd: int = KOHLER_N4):
+def analyze_host(img, M: int, max_k: int, nbhd: int = KOHLER_N4, out=None):
     """Whole path from a host image (numpy array or CPU tensor, pinned is fastest) back
-    to host results: (card, sumc, curve, thresholds, count, t0) as numpy arrays."""
+    to host results: (card, sumc, curve, thresholds, count, t0) as numpy arrays and ints.
+    `out` (from host_outputs(M, max_k)) supplies the output arrays, for callers that
+    repeat the call without allocating."""
     import numpy as np
 
     if isinstance(img, torch.Tensor):
@@ -213,16 +215,32 @@ def analyze_host(img, M: int, max_k: int, nbhd: int = KOHLER_N4):
             raise ValueError("host image must be a 2-D uint8/uint16 array with unit stride along rows")
         code = KOHLER_U8 if a.dtype == np.uint8 else KOHLER_U16
         ptr, w, h, pitch = a.ctypes.data, a.shape[1], a.shape[0], a.strides[0]
-    card = np.empty(M, np.uint64)
-    sumc = np.empty(M, np.uint64)
-    c = np.empty(M, np.float64)
-    ts = np.empty(max(max_k, 1), np.int32)
-    cnt = np.zeros(1, np.int32)
-    t0 = np.zeros(1, np.int32)
+    if out is not None:
+        card, sumc, c, ts, cnt, t0 = out[0], out[1], out[2], out[3], out[4], out[5]
+        if (card.shape != (M,) or sumc.shape != (M,) or c.shape != (M,) or ts.size < max_k
+                or card.dtype != np.uint64 or sumc.dtype != np.uint64 or c.dtype != np.float64
+                or ts.dtype != np.int32 or not isinstance(cnt, np.ndarray) or not isinstance(t0, np.ndarray)):
+            raise ValueError("out must come from host_outputs(M, max_k) with the call's M and max_k")
+    else:
+        card = np.empty(M, np.uint64)
+        sumc = np.empty(M, np.uint64)
+        c = np.empty(M, np.float64)
+        ts = np.empty(max(max_k, 1), np.int32)
+        cnt = np.zeros(1, np.int32)
+        t0 = np.zeros(1, np.int32)
     _check(lib().kohler_analyze_host(ptr, code, w, h, pitch, M, nbhd, max_k, card.ctypes.data,
                                      sumc.ctypes.data, c.ctypes.data, ts.ctypes.data, cnt.ctypes.data,
                                      t0.ctypes.data), "kohler_analyze_host")
     return card, sumc, c, ts[:max_k], int(cnt[0]), int(t0[0])
+
+
+def host_outputs(M: int, max_k: int):
+    """Output arrays for analyze_host(..., out=...): card, sumc (uint64[M]), curve
+    (float64[M]), thresholds (int32[max(max_k, 1)]), count and t0 (int32[1])."""
+    import numpy as np
+
+    return (np.empty(M, np.uint64), np.empty(M, np.uint64), np.empty(M, np.float64),
+            np.empty(max(max_k, 1), np.int32), np.zeros(1, np.int32), np.zeros(1, np.int32))
 
 
 def segment(img: torch.Tensor, M: int, thresholds: torch.Tensor, count: torch.Tensor = None, *, out=None,

@@ -973,7 +973,8 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   // device outputs: card, sumc (uint64 M), curve (double M), out_t (max_k), count, t0
   const size_t o_card = 0, o_sumc = (size_t)M * 8, o_curve = 2 * (size_t)M * 8, o_t = 3 * (size_t)M * 8;
   const size_t o_cnt = o_t + ((size_t)std::max(max_k, 1) * 4 + 15) / 16 * 16, o_t0 = o_cnt + 16;
-  const size_t out_bytes = o_t0 + 16;
+  const size_t o_sticky = o_t0 + 16;  // host mirror only: the stream's error word
+  const size_t out_bytes = o_sticky + 16;
   // The image is copied to the device in bands by the copy engine (pinned
   // memory: asynchronously), each band reduced while the next one is copied.
   // Reading pinned memory from the pass itself, over the host link, is about
@@ -984,8 +985,10 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   const int64_t dpitch = packed ? width * es : ((width * es + 127) / 128) * 128;
   const size_t img_bytes = (size_t)dpitch * height;
   // bands of rows: copy band b + 1 while band b is reduced (a band needs the first
-  // row of the next band for its lower pairs)
-  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(8, img_bytes / (2 << 20)));
+  // row of the next band for its lower pairs).  Each band costs four host calls
+  // (copy, event, wait, launch) of several microseconds each, so bands are at
+  // least 8 MB: one per 8 MB, at most 4.
+  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(4, img_bytes / (8 << 20)));
   std::lock_guard<std::mutex> lock(g_host_mu);
   HostPath* h = nullptr;
   rc = host_path(&h, img_bytes, out_bytes, nbands + 1);
@@ -1027,12 +1030,26 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
       if (rc) return rc;
     }
   }
-  // results back to the host: one copy into the pinned mirror, then host copies
-  e = cudaMemcpyAsync(h->hout, dout, out_bytes, cudaMemcpyDeviceToHost, h->compute);
+  // results and the stream's error word back to the host in one wait: copies into
+  // the pinned mirror, then host copies
+  Workspace* ws = nullptr;
+  rc = get_workspace(h->compute, 1, 128, cand_ints(2), &ws);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(h->hout, dout, o_sticky, cudaMemcpyDeviceToHost, h->compute);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(h->hout) + o_sticky, ws->sticky, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                        h->compute);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->compute);
   if (e != cudaSuccess) return status_of(e);
-  rc = kohler_stream_status(h->compute);  // waits for the stream
-  if (rc != KOHLER_OK && rc != KOHLER_ERR_RANGE) return rc;
   const char* ho = static_cast<const char*>(h->hout);
+  unsigned bits = 0;
+  memcpy(&bits, ho + o_sticky, sizeof(bits));
+  if (bits) {
+    e = cudaMemset(ws->sticky, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return status_of(e);
+  }
+  if (bits & kErrInternal) return KOHLER_ERR_CUDA;
+  rc = (bits & kErrRange) ? KOHLER_ERR_RANGE : KOHLER_OK;
   struct Cp {
     void* dst;
     size_t off, bytes;

@@ -141,7 +141,7 @@ def test_host_path_and_curve_api(nb):
 def test_host_path_in_bands(nb):
     # an image large enough to be copied in several bands (band edges inside the image)
     k = K()
-    img = synth.voronoi_image(9, 1536, 2731, 64, 4.0)
+    img = synth.voronoi_18mp()
     got = k.analyze_host(img, 256, MAX_K, nbhd=nb)
     assert_same(got, oracle.analyze(img, 256, MAX_K, nbhd=nb))
 

@@ -340,6 +340,11 @@ def test_analyze_host(shape):
     pinned = torch.from_numpy(img).pin_memory()
     got = k.analyze_host(pinned, 256, MAX_K)
     assert_same(got, expect(img, 256))
+    out = k.host_outputs(256, MAX_K)
+    for _ in range(2):  # the caller's arrays, reused
+        assert_same(k.analyze_host(pinned, 256, MAX_K, out=out), expect(img, 256))
+    with pytest.raises(ValueError):
+        k.analyze_host(pinned, 256, MAX_K, out=k.host_outputs(255, MAX_K))
 
 
 @pytest.mark.parametrize("dtype,w,h,M", [(np.uint8, 1000, 600, 256), (np.uint8, 333, 101, 200), (np.uint16, 516, 130, 4096)])
@@ -355,10 +360,27 @@ def test_analyze_host_u16_and_range():
     k = K()
     img = synth.smooth_image(8, 200, 150, 4096, np.uint16, noise_sd=25.0)
     assert_same(k.analyze_host(img, 4096, MAX_K), expect(img, 4096))
-    img[10, 10] = 4096
+    bad = img.copy()
+    bad[10, 10] = 4096
     with pytest.raises(k.KohlerError) as e:
-        k.analyze_host(img, 4096, MAX_K)
+        k.analyze_host(bad, 4096, MAX_K)
     assert e.value.status == k.ERR_RANGE
+    # the error is reported once: the next call on a clean image succeeds
+    assert_same(k.analyze_host(img, 4096, MAX_K), expect(img, 4096))
+
+
+def test_analyze_host_in_bands():
+    # images of more than 8 MB are copied and reduced in row bands (one per 8 MB,
+    # at most 4): 36 Mpx pinned and packed (4 bands), and 18 Mpx from a wider
+    # array (rows copied to a padded device pitch, 2 bands)
+    k = K()
+    big = synth.random_image(12, 6016, 6000, 256)
+    got = k.analyze_host(torch.from_numpy(big).pin_memory(), 256, MAX_K)
+    assert_same(got, expect(big, 256), "36 Mpx")
+    wide = np.zeros((3456, 5200), np.uint8)
+    wide[:, :5184] = synth.voronoi_18mp()
+    view = wide[:, :5184]
+    assert_same(k.analyze_host(view, 256, MAX_K), expect(np.ascontiguousarray(view), 256), "18 Mpx, pitch 5200")
 
 
 # ------------------------------------------------------------------------ workloads at full size
