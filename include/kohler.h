@@ -14,6 +14,8 @@
  * Eq. 4).  Only pairs with both pixels inside the image exist.  Section 3.2
  * (Eq. 7-9) shows that scanning each unordered neighbour pair once (right and
  * lower neighbour, the half neighbourhood N4*) gives the same card and sumc.
+ * The `nb` argument selects the 4-, 8- or hexagonal 6-neighbourhood instead
+ * (kohler_nbhd below); the definitions are otherwise the same.
  *
  * Exactness: card and sumc are exact unsigned 64-bit integers.  C(t) is the
  * IEEE-754 double quotient, rounded to nearest, of the two integers converted to

@@ -35,7 +35,7 @@ namespace kohler {
 
 constexpr int kMaxBatch = 128;      // images per launch (descriptors travel in kernel parameters, ~7 KB)
 constexpr int kEpiThreads = 256;    // threads of the epilogue / threshold block
-constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, warp winners, per-warp top lists
+constexpr int kShInts = 40 + 32 * 32;  // small shared ints of a block: flags, radix-select counters, candidate list
 constexpr int kScratch = 3 * 33;       // shared uint64 scratch of a block (block scans of up to 3 values)
 
 // Ints of threshold-candidate scratch for M levels: up to (M + 1) / 2 + 1
@@ -98,10 +98,6 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b) {
   uint32_t r;
   asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "n"(SEL));
   return r;
-}
-
-__device__ __forceinline__ unsigned long long ldcg_u64(const unsigned long long* p) {
-  return __ldcg(p);
 }
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
