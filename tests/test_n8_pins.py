@@ -2,6 +2,7 @@
 from the oracle itself (the paper states the method for N4 and notes that the 8-
 or 6-neighbourhood gives insignificant differences; Eq. 1-3 carry over with N8).
 
+- a hand-worked 2 x 2 example with both diagonal pairs,
 - a brute force that builds B(t) as an explicit list of ordered 8-neighbour pairs,
 - closed forms: vertical and horizontal steps (3H - 2 and 3W - 2 boundary pairs),
   a checkerboard (its diagonal pairs are equal, so N8 gives the N4 curve),
@@ -26,8 +27,24 @@ def _n8star_pairs(img):
     return np.concatenate(a), np.concatenate(b)
 
 
+# Hand-worked: rows (0 4) and (6 9).  Unordered N8* pairs (lo, hi): (0,4) (6,9)
+# right, (0,6) (4,9) down, (0,9) down-right, (4,6) down-left.  Per t, the pairs
+# with lo <= t < hi and their min(hi - t, t - lo):
+#   t=0: (0,4):0 (0,6):0 (0,9):0                 t=5: (0,6):1 (4,9):1 (4,6):1 (0,9):4
+#   t=1: (0,4):1 (0,6):1 (0,9):1                 t=6: (6,9):0 (4,9):2 (0,9):3
+#   t=2: (0,4):2 (0,6):2 (0,9):2                 t=7: (6,9):1 (4,9):2 (0,9):2
+#   t=3: (0,4):1 (0,6):3 (0,9):3                 t=8: (6,9):1 (4,9):1 (0,9):1
+#   t=4: (0,6):2 (4,9):0 (4,6):0 (0,9):4         t=9: none
+HAND_IMG = np.array([[0, 4], [6, 9]], np.uint8)
+HAND_CARD = [3, 3, 3, 3, 4, 4, 3, 3, 3, 0]
+HAND_SUMC = [0, 3, 6, 7, 6, 7, 5, 5, 3, 0]
+
+
 def _n8_suite(curve_fn):
     fails = []
+    card, sumc = curve_fn(HAND_IMG, 10)
+    if list(card) != HAND_CARD or list(sumc) != HAND_SUMC:
+        fails.append("hand2x2")
     a_, b_ = 20, 29
     for H, W, vertical in ((5, 6, True), (4, 9, False), (1, 4, True), (6, 1, False)):
         img = np.full((H, W), a_, np.uint8)
@@ -60,6 +77,11 @@ def _n8_suite(curve_fn):
     if int(np.sum(card)) != int(d.sum()) or int(np.sum(sumc)) != int((d * d // 4).sum()):
         fails.append("sums")
     return fails
+
+
+def test_brute_force_agrees_with_the_hand_example():
+    card, sumc = brute.curve(HAND_IMG, 10, nbhd=8)
+    assert card == HAND_CARD and sumc == HAND_SUMC
 
 
 @pytest.mark.parametrize("route", ["n8", "n8half", "n8_alg1"])
