@@ -735,7 +735,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
 
     # the comparisons run in their own thread, off the poll path; it frees the slot
     checks = queue.Queue()
-    verdict = [True]
+    all_equal = [True]
 
     def checker():
         while True:
@@ -743,7 +743,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
             if item is None:
                 return
             r, k, slot, t0 = item
-            verdict[0] = verdict[0] and t0 == want[(r, k)][0] and np.array_equal(outs[r][slot], want_seg[(r, k)])
+            all_equal[0] = all_equal[0] and t0 == want[(r, k)][0] and np.array_equal(outs[r][slot], want_seg[(r, k)])
             free[r].release()
 
     th = threading.Thread(target=producer)
@@ -760,7 +760,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
     t_end = time.perf_counter()
     checks.put(None)
     tc.join()
-    seg_ok = verdict[0]
+    seg_ok = all_equal[0]
     srv.close()
     out["segmented_open_loop"] = {"fps_achieved": n_frames / (t_end - t_base),
                                   "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
