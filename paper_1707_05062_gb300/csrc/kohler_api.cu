@@ -63,15 +63,16 @@ EncodeTiled encode_tiled() {
   return fn;
 }
 
-// Tensor map of a uint8 image for the strip pass: rows of W / 2 uint16 elements
-// (pixel pairs), `pitch` bytes apart; boxes of 136 elements (a 256-column strip
-// and its 16-byte right halo) by 4 rows; reads outside the image give zeros.
-int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int64_t pitch) {
+// Tensor map of a uint8 image for the strip passes: rows of W / 2 uint16
+// elements (pixel pairs), `pitch` bytes apart; boxes of box_w elements (136: a
+// 256-column strip and its 16-byte right halo; 144: also a 16-byte left halo)
+// by 4 rows; reads outside the image give zeros.
+int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int64_t pitch, uint32_t box_w) {
   EncodeTiled enc = encode_tiled();
   if (!enc) return KOHLER_ERR_CUDA;
   const cuuint64_t dims[2] = {(cuuint64_t)(W / 2), (cuuint64_t)H};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  const cuuint32_t box[2] = {u8h::kBoxW, (cuuint32_t)u8h::kGroupRows};
+  const cuuint32_t box[2] = {box_w, (cuuint32_t)u8h::kGroupRows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -156,8 +157,16 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
 enum class Pass {
   HistU8, HistU8Check, FastU8, FastU8Check, FastU16, GenericU8, GenericU16, GlobalU8, GlobalU16,
   // the 8- and hexagonal 6-neighbourhoods (general per-pair route)
-  GenericU8N8, GenericU16N8, GlobalU16N8, GenericU8N6, GenericU16N6, GlobalU16N6
+  GenericU8N8, GenericU16N8, GlobalU16N8, GenericU8N6, GenericU16N6, GlobalU16N6,
+  // the 8- and hexagonal 6-neighbourhoods on 16-byte aligned uint8 rows (strip pass)
+  HistU8N8, HistU8N8Check, HistU8N6, HistU8N6Check
 };
+
+// The strip passes (2-D tensor copies of 16-byte aligned uint8 rows).
+bool is_strip(Pass p) {
+  return p == Pass::HistU8 || p == Pass::HistU8Check || p == Pass::HistU8N8 || p == Pass::HistU8N8Check ||
+         p == Pass::HistU8N6 || p == Pass::HistU8N6Check;
+}
 
 // Passes that add straight to the global histograms (M above the shared-memory bins).
 bool is_global(Pass p) {
@@ -187,16 +196,19 @@ int check_common(kohler_dtype dt, int32_t M, kohler_nbhd nb) {
 }
 
 Pass pass_for(const kohler_image& im, kohler_dtype dt, int M, kohler_nbhd nb) {
+  const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
+  const bool aligned16 = (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0);
+  const bool strip = dt == KOHLER_U8 && aligned16 && im.width % 16 == 0;
   if (nb == KOHLER_N8) {
+    if (strip) return M == 256 ? Pass::HistU8N8 : Pass::HistU8N8Check;
     if (dt == KOHLER_U8) return Pass::GenericU8N8;
     return M > kMaxSmemBins ? Pass::GlobalU16N8 : Pass::GenericU16N8;
   }
   if (nb == KOHLER_N6) {
+    if (strip) return M == 256 ? Pass::HistU8N6 : Pass::HistU8N6Check;
     if (dt == KOHLER_U8) return Pass::GenericU8N6;
     return M > kMaxSmemBins ? Pass::GlobalU16N6 : Pass::GenericU16N6;
   }
-  const bool aligned8 = (((uintptr_t)im.img & 7) == 0) && ((im.pitch_bytes & 7) == 0);
-  const bool aligned16 = (((uintptr_t)im.img & 15) == 0) && ((im.pitch_bytes & 15) == 0);
   if (dt == KOHLER_U8) {
     if (aligned16 && im.width % 16 == 0) return M == 256 ? Pass::HistU8 : Pass::HistU8Check;
     if (aligned8 && im.width % 8 == 0) return M == 256 ? Pass::FastU8 : Pass::FastU8Check;
@@ -211,7 +223,11 @@ Pass pass_for(const kohler_image& im, kohler_dtype dt, int M, kohler_nbhd nb) {
 int strip_px(Pass p, int px) {
   switch (p) {
     case Pass::HistU8:
-    case Pass::HistU8Check: return u8h::kStripPx;
+    case Pass::HistU8Check:
+    case Pass::HistU8N8:
+    case Pass::HistU8N8Check:
+    case Pass::HistU8N6:
+    case Pass::HistU8N6Check: return u8h::kStripPx;
     case Pass::FastU8:
     case Pass::FastU8Check: return u8r::kStripPx;
     case Pass::FastU16: return 32 * px;
@@ -260,6 +276,18 @@ KernelInfo kernel_for(Pass p, int bins, bool single, int warps = kFastWarps, int
     case Pass::GenericU8N6: return {(const void*)k_generic<1, false, 6>, kGenericWarps * 32, (size_t)bins * 4 * 4};
     case Pass::GenericU16N6: return {(const void*)k_generic<2, false, 6>, kGenericWarps * 32, (size_t)bins * 4 * 4};
     case Pass::GlobalU16N6: return {(const void*)k_generic<2, true, 6>, kGenericWarps * 32, 0};
+    case Pass::HistU8N8:
+      return {single ? (const void*)k_u8n<false, 1, 8> : (const void*)k_u8n<false, kMaxBatch, 8>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
+    case Pass::HistU8N8Check:
+      return {single ? (const void*)k_u8n<true, 1, 8> : (const void*)k_u8n<true, kMaxBatch, 8>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
+    case Pass::HistU8N6:
+      return {single ? (const void*)k_u8n<false, 1, 6> : (const void*)k_u8n<false, kMaxBatch, 6>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
+    case Pass::HistU8N6Check:
+      return {single ? (const void*)k_u8n<true, 1, 6> : (const void*)k_u8n<true, kMaxBatch, 6>, u8h::kNW * 32,
+              (size_t)u8h::kDynBytes};
   }
   return {nullptr, 0, 0};
 }
@@ -328,9 +356,7 @@ struct Band {
 
 // Rows per work unit: the uint8 pass works on units of 8 rows of a strip, the
 // others on rows.
-bool is_fast_u8(Pass p) {
-  return p == Pass::HistU8 || p == Pass::HistU8Check || p == Pass::FastU8 || p == Pass::FastU8Check;
-}
+bool is_fast_u8(Pass p) { return is_strip(p) || p == Pass::FastU8 || p == Pass::FastU8Check; }
 int unit_rows(Pass p) { return is_fast_u8(p) ? u8r::kUnitRows : 1; }
 
 // What an image's completion counter counts to: the uint8 pass reports
@@ -341,12 +367,13 @@ uint32_t completion_total(Pass p, int64_t strips, int64_t H) {
 }
 
 // Names of the passes in tuning files and reports (in the order of Pass).
-constexpr const char* kPassNames[] = {"u8_strip",       "u8_strip_check", "u8_row",         "u8_row_check",
-                                      "u16_fast",       "u8_generic",     "u16_generic",    "u8_global",
-                                      "u16_global",     "u8_generic_n8",  "u16_generic_n8", "u16_global_n8",
-                                      "u8_generic_n6",  "u16_generic_n6", "u16_global_n6"};
+constexpr const char* kPassNames[] = {"u8_strip",          "u8_strip_check",    "u8_row",         "u8_row_check",
+                                      "u16_fast",          "u8_generic",        "u16_generic",    "u8_global",
+                                      "u16_global",        "u8_generic_n8",     "u16_generic_n8", "u16_global_n8",
+                                      "u8_generic_n6",     "u16_generic_n6",    "u16_global_n6",  "u8_strip_n8",
+                                      "u8_strip_n8_check", "u8_strip_n6",       "u8_strip_n6_check"};
 constexpr int kNumPasses = (int)(sizeof(kPassNames) / sizeof(kPassNames[0]));
-static_assert(kNumPasses == (int)Pass::GlobalU16N6 + 1, "one name per pass");
+static_assert(kNumPasses == (int)Pass::HistU8N6Check + 1, "one name per pass");
 
 // Routes that a group whose images take pass p may take instead: each one is
 // correct for every image that p accepts (its alignment, width and M rules are
@@ -359,6 +386,10 @@ bool route_ok(Pass p, Pass r) {
     case Pass::FastU8:
     case Pass::FastU8Check: return r == Pass::GenericU8;
     case Pass::FastU16: return r == Pass::GenericU16;
+    case Pass::HistU8N8:
+    case Pass::HistU8N8Check: return r == Pass::GenericU8N8;
+    case Pass::HistU8N6:
+    case Pass::HistU8N6Check: return r == Pass::GenericU8N6;
     default: return false;
   }
 }
@@ -451,18 +482,19 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cudaError_t e;
-  if ((route == Pass::HistU8 || route == Pass::HistU8Check) && P.n == 1) {
+  const uint32_t box_w = (route == Pass::HistU8 || route == Pass::HistU8Check) ? u8h::kBoxW : u8n::kBoxW;
+  if (is_strip(route) && P.n == 1) {
     // one image: the kernel instance that takes a single tensor map
     ImgMaps<1> T1;
-    const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch);
+    const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch, box_w);
     if (rc) return rc;
     void* args[] = {&P, &T1};
     e = cudaLaunchKernelExC(&cfg, k.fn, args);
-  } else if (route == Pass::HistU8 || route == Pass::HistU8Check) {
+  } else if (is_strip(route)) {
     static thread_local ImgMaps<kMaxBatch> T;  // 16 KB: kept off the stack
     for (int j = 0; j < P.n; ++j) {
       const ImgDesc& d = P.img[j];
-      const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch);
+      const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch, box_w);
       if (rc) return rc;
     }
     void* args[] = {&P, &T};

@@ -5,5 +5,6 @@
 #include "kohler_u16.cuh"
 #include "kohler_u8r.cuh"
 #include "kohler_u8h.cuh"
+#include "kohler_u8n.cuh"
 #include "kohler_pairs.cuh"
 #include "kohler_thresholds.cuh"

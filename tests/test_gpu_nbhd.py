@@ -124,6 +124,38 @@ def test_n6_row_parity_comes_from_the_image_row():
     assert_same(crop, oracle.analyze(np.ascontiguousarray(img[1:]), 256, MAX_K, nbhd=6))
 
 
+# 16-byte aligned uint8 rows with W % 16 == 0 take the strip pass (tensor copies
+# with left and right halos): ragged last strips, 1- and 2-row images, M < 256
+STRIP_SHAPES = [(1, 16), (2, 16), (3, 32), (3, 272), (5, 512), (50, 528), (129, 784), (33, 4112), (2, 1296)]
+
+
+@NBS
+@pytest.mark.parametrize("h,w", STRIP_SHAPES)
+@pytest.mark.parametrize("kind", ["smooth", "random"])
+def test_strip_route_shapes(h, w, kind, nb):
+    seed = 5 * h + w
+    img = synth.smooth_image(seed, w, h, 256) if kind == "smooth" else synth.random_image(seed, w, h, 256)
+    assert_same(run([img], 256, nb)[0], oracle.analyze(img, 256, MAX_K, nbhd=nb), f"{h}x{w}")
+
+
+@NBS
+@pytest.mark.parametrize("M", [2, 61, 200])
+def test_strip_route_small_M(M, nb):
+    img = synth.smooth_image(M + 3, 528, 45, M)
+    assert_same(run([img], M, nb)[0], oracle.analyze(img, M, MAX_K, nbhd=nb), f"M={M}")
+
+
+@NBS
+def test_strip_route_batch_and_crop(nb):
+    # several strip images in one launch (one tensor map each), and a crop that
+    # starts one row lower (the N6 row parity follows the image's own rows)
+    imgs = [synth.random_image(k, w, h, 256) for k, (h, w) in enumerate([(64, 256), (3, 528), (77, 1024)])]
+    imgs.append(np.ascontiguousarray(imgs[2][1:]))
+    got = run(imgs, 256, nb)
+    for i, im in enumerate(imgs):
+        assert_same(got[i], oracle.analyze(im, 256, MAX_K, nbhd=nb), f"image {i}")
+
+
 @NBS
 def test_host_path_and_curve_api(nb):
     k = K()
