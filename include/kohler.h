@@ -63,8 +63,9 @@ typedef enum { KOHLER_U8 = 1, KOHLER_U16 = 2 } kohler_dtype;
  *              shifted half a pixel to the right: the left and right pixels,
  *              and in the rows above and below columns x - 1 and x on an even
  *              row, x and x + 1 on an odd row.
- * N8 and N6 are computed on a general per-pair route; the frame server is N4
- * only.  Other values: KOHLER_ERR_UNSUPPORTED. */
+ * N8 and N6 take a strip pass for uint8 images whose base, pitch and width are
+ * multiples of 16 bytes, and a general per-pair route otherwise; the frame
+ * server is N4 only.  Other values: KOHLER_ERR_UNSUPPORTED. */
 typedef enum { KOHLER_N4 = 4, KOHLER_N6 = 6, KOHLER_N8 = 8 } kohler_nbhd;
 
 typedef enum {
