@@ -39,7 +39,12 @@
  *    next multiple of 8 bytes; those bytes never change a result.
  *  - Every call returns a kohler_status; none aborts.  A pixel value >= M is
  *    found on the device: that image's outputs are all zero and the next
- *    kohler_stream_status() on the stream returns KOHLER_ERR_RANGE.
+ *    kohler_stream_status() on the stream returns KOHLER_ERR_RANGE.  A wait of
+ *    the kernels on their own data copies that gives up (bounded; it does not
+ *    happen on a working GPU) zeroes that image's outputs the same way and makes
+ *    the next kohler_stream_status() return KOHLER_ERR_CUDA.
+ *  - A call's first kernel starts after the work enqueued before it on the
+ *    stream has finished, unless kohler_stream_overlap() allows the overlap.
  */
 #ifndef KOHLER_H
 #define KOHLER_H
@@ -160,12 +165,44 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
  * into a CUDA graph.  Each call clears the array on `cuda_stream` before use.
  * All calls share the one array, so calls whose work overlaps on the GPU
  * (different streams, or two host threads) race; serialize them.
- * out_status: device int32[1], KOHLER_OK or KOHLER_ERR_RANGE (pixel >= M, outputs
- * all zero); other outputs as in kohler_analyze_batch for n = 1. */
+ * out_status: device int32[1], KOHLER_OK, KOHLER_ERR_RANGE (pixel >= M, outputs
+ * all zero) or KOHLER_ERR_CUDA (a wait of the kernel for its own data copies
+ * gave up, outputs all zero); other outputs as in kohler_analyze_batch for
+ * n = 1.  The call's kernels may start while the stream's previous kernel
+ * ends (after the array is cleared on the stream, see kohler_stream_overlap). */
 int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int64_t height, int64_t pitch_bytes,
                            int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve,
                            int32_t* out_t, int32_t* out_count, int32_t* out_t0, int32_t* out_status,
                            void* cuda_stream);
+
+/* Allows (enable = 1) or forbids (0, the default) the first kernel of each later
+ * call on `cuda_stream` of the current device to start before the stream's
+ * previous kernel has finished (programmatic dependent launch).  The library's
+ * kernels read their images at once but write global memory only after the
+ * previous kernel has finished, so back-to-back calls overlap one call's
+ * epilogue with the next call's pass.  Allow it only when the stream's kernel
+ * right before each call does not write that call's images (for instance,
+ * when it is the library's own previous call, or when the images were written
+ * before it).  The library's internal streams (server, host path) allow it.
+ * Calls on other streams are unaffected.  The paper has no counterpart: this
+ * is a scheduling choice of this implementation. */
+int kohler_stream_overlap(void* cuda_stream, int32_t enable);
+
+/* Test hooks (the paper has no counterpart).  They make failures happen on the
+ * host side, so that error paths can be tested without faulting a GPU:
+ *   KOHLER_FAULT_ALLOC: the next `count` device or pinned allocations of the
+ *     library (workspaces, host-path buffers, server buffers and slots,
+ *     segmentation scratch) fail as if out of memory, without allocating; the
+ *     call that needed them returns KOHLER_ERR_NOMEM (a server frame finishes
+ *     with it) and leaves no partial state behind.
+ *   KOHLER_FAULT_RING_WAIT: in each of the next `count` launches of the uint8
+ *     strip pass (4-neighbourhood), one warp treats a completed wait for its
+ *     data as failed, exactly as a wait that gave up: the launch's first image
+ *     reports KOHLER_ERR_CUDA (out_status, server frame status, and
+ *     kohler_stream_status) and its outputs are zero.
+ * count = 0 cancels.  KOHLER_ERR_ARG for another kind or count < 0. */
+enum { KOHLER_FAULT_ALLOC = 1, KOHLER_FAULT_RING_WAIT = 2 };
+int kohler_test_inject(int32_t kind, int32_t count);
 
 /* Waits for `cuda_stream` and returns the deferred status of the calls enqueued
  * on it since the previous kohler_stream_status: KOHLER_ERR_RANGE if an image had

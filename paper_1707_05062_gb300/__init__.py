@@ -65,6 +65,8 @@ def lib():
             L.kohler_analyze_batch.argtypes = [p, i32, i, i32, i, i32, p, p, p, p, p, p, p]
             L.kohler_analyze_host.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p]
             L.kohler_stream_status.argtypes = [p]
+            L.kohler_stream_overlap.argtypes = [p, i32]
+            L.kohler_test_inject.argtypes = [i32, i32]
             L.kohler_segment.argtypes = [p, i, i64, i64, i64, i32, p, p, i32, p, i64, p]
             if hasattr(L, "kohler_analyze_noalloc"):
                 L.kohler_analyze_noalloc.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p, p, p]
@@ -81,7 +83,8 @@ def lib():
             L.kohler_strerror.argtypes = [i]
             L.kohler_strerror.restype = ctypes.c_char_p
             for name in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_analyze_batch",
-                         "kohler_analyze_host", "kohler_stream_status", "kohler_release", "kohler_segment"):
+                         "kohler_analyze_host", "kohler_stream_status", "kohler_release", "kohler_segment",
+                         "kohler_stream_overlap", "kohler_test_inject"):
                 getattr(L, name).restype = i
             if hasattr(L, "kohler_server_create"):
                 L.kohler_server_create.argtypes = [p, i32, i32, ctypes.c_size_t, i32]
@@ -97,6 +100,22 @@ def lib():
                     getattr(L, name).restype = i
             _lib = L
     return _lib
+
+
+FAULT_ALLOC, FAULT_RING_WAIT = 1, 2
+
+
+def stream_overlap(stream=None, enable: bool = True):
+    """Lets the first kernel of each later call on `stream` start before the
+    stream's previous kernel ends (kohler_stream_overlap): only for streams
+    whose kernel before each call does not write that call's images."""
+    _check(lib().kohler_stream_overlap(_stream(stream), 1 if enable else 0), "kohler_stream_overlap")
+
+
+def test_inject(kind: int, count: int):
+    """Test hook (kohler_test_inject): host-side injected allocation failures
+    (FAULT_ALLOC) or ring-wait failures of the strip pass (FAULT_RING_WAIT)."""
+    _check(lib().kohler_test_inject(kind, count), "kohler_test_inject")
 
 
 def _check(rc: int, what: str):

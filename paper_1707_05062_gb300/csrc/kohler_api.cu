@@ -8,8 +8,10 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <map>
 #include <mutex>
+#include <set>
 #include <string>
 #include <tuple>
 #include <utility>
@@ -66,13 +68,14 @@ EncodeTiled encode_tiled() {
 // Tensor map of a uint8 image for the strip passes: rows of W / 2 uint16
 // elements (pixel pairs), `pitch` bytes apart; boxes of box_w elements (136: a
 // 256-column strip and its 16-byte right halo; 144: also a 16-byte left halo)
-// by 4 rows; reads outside the image give zeros.
-int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int64_t pitch, uint32_t box_w) {
+// by box_h rows; reads outside the image give zeros.
+int encode_u8_rows(CUtensorMap* map, const void* base, int64_t W, int64_t H, int64_t pitch, uint32_t box_w,
+                   uint32_t box_h) {
   EncodeTiled enc = encode_tiled();
   if (!enc) return KOHLER_ERR_CUDA;
   const cuuint64_t dims[2] = {(cuuint64_t)(W / 2), (cuuint64_t)H};
   const cuuint64_t strides[1] = {(cuuint64_t)pitch};
-  const cuuint32_t box[2] = {box_w, (cuuint32_t)u8h::kGroupRows};
+  const cuuint32_t box[2] = {box_w, box_h};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
@@ -130,7 +133,7 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
   const size_t cand_b = align256((size_t)slots * cand_stride * sizeof(int32_t));
   const size_t total = hist_b + done_b + err_b + sticky_b + cand_b;
   void* mem = nullptr;
-  e = cudaMalloc(&mem, total);
+  e = kohler::dev_malloc(&mem, total);
   if (e != cudaSuccess) {
     w->slots = w->hist_words = w->cand_stride = 0;
     return status_of(e);
@@ -258,11 +261,11 @@ const void* fast_u16_fn(int warps, int px) {
 KernelInfo kernel_for(Pass p, int bins, bool single, int warps = kFastWarps, int px = 4) {
   switch (p) {
     case Pass::HistU8:
-      return {single ? (const void*)k_u8h<false, 1> : (const void*)k_u8h<false, kMaxBatch>, u8h::kNW * 32,
-              (size_t)u8h::kDynBytes};
+      return {single ? (const void*)k_u8h<false, 1, true> : (const void*)k_u8h<false, kMaxBatch, true>,
+              u8h::kNW * 32, (size_t)u8h::kDynBytes};
     case Pass::HistU8Check:
-      return {single ? (const void*)k_u8h<true, 1> : (const void*)k_u8h<true, kMaxBatch>, u8h::kNW * 32,
-              (size_t)u8h::kDynBytes};
+      return {single ? (const void*)k_u8h<true, 1, true> : (const void*)k_u8h<true, kMaxBatch, true>,
+              u8h::kNW * 32, (size_t)u8h::kDynBytes};
     case Pass::FastU8: return {(const void*)k_u8r<false>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU8Check: return {(const void*)k_u8r<true>, u8r::kNW * 32, (size_t)u8r::kWords * 4};
     case Pass::FastU16: return {fast_u16_fn(warps, px), warps * 32, (size_t)bins * 5 * 4};
@@ -415,9 +418,16 @@ int px_class_of(int64_t pixels) {
 // `idx` (indices into imgs); slots = position in the launch.  The launch
 // parameters are `force` if given, else the tuned entry for this kind of group,
 // else the defaults.
+// `chained`: on entry, whether the stream's previous kernel is known to leave
+// the images alone (the library's own launch earlier in this call, or the
+// caller allowed the overlap with kohler_stream_overlap); then the pass may
+// start before that kernel ends (programmatic dependent launch: it reads its
+// images at once and waits for the previous kernel only before its first
+// global write).  Otherwise the pass starts after the previous work on the
+// stream.  Set on return.
 int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* imgs, const std::vector<Band>* bands,
                  int M, int bins, Workspace* ws, LaunchParams& base, cudaStream_t stream, const std::vector<int>& slot_of,
-                 const int* out_index, const TuneVal* force = nullptr) {
+                 const int* out_index, bool& chained, const TuneVal* force = nullptr) {
   if (idx.empty()) return KOHLER_OK;
   int64_t pixels = 0;
   bool vec16 = true;  // every image allows 8 uint16 pixels per lane (16-byte loads)
@@ -466,11 +476,14 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   P.bins = bins;
   P.M = M;
   KernelInfo k = kernel_for(route, bins, P.n == 1, t.warps, t.px);
-  k.smem = std::max(k.smem, epilogue_smem(M, bins, k.smem));
-  P.smem_bytes = (int32_t)k.smem;
+  // the 4-neighbourhood strip pass leaves the epilogue to k_finish; the
+  // other passes run it in the block that completes an image
+  const bool split = route == Pass::HistU8 || route == Pass::HistU8Check;
+  const size_t epi = epilogue_smem(M, bins, split ? 0 : k.smem);
+  if (!split) k.smem = std::max(k.smem, epi);
+  P.smem_bytes = (int32_t)(split ? epi : k.smem);
+  if (split && kohler::take_wait_fault()) P.fail_wait = 1u;
   const int grid = grid_for(k, rs, t.upw, t.per_sm);
-  // programmatic dependent launch: this pass may start while the previous
-  // kernel on the stream finishes (it waits for it before writing global memory)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(k.threads);
@@ -480,13 +493,14 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = chained ? 1 : 0;
   cudaError_t e;
-  const uint32_t box_w = (route == Pass::HistU8 || route == Pass::HistU8Check) ? u8h::kBoxW : u8n::kBoxW;
+  const uint32_t box_w = split ? u8h::kBoxW : u8n::kBoxW;
+  const uint32_t box_h = (uint32_t)u8h::kGroupRows;
   if (is_strip(route) && P.n == 1) {
     // one image: the kernel instance that takes a single tensor map
     ImgMaps<1> T1;
-    const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch, box_w);
+    const int rc = encode_u8_rows(&T1.map[0], P.img[0].base, P.img[0].W, P.img[0].H, P.img[0].pitch, box_w, box_h);
     if (rc) return rc;
     void* args[] = {&P, &T1};
     e = cudaLaunchKernelExC(&cfg, k.fn, args);
@@ -494,7 +508,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
     static thread_local ImgMaps<kMaxBatch> T;  // 16 KB: kept off the stack
     for (int j = 0; j < P.n; ++j) {
       const ImgDesc& d = P.img[j];
-      const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch, box_w);
+      const int rc = encode_u8_rows(&T.map[j], d.base, d.W, d.H, d.pitch, box_w, box_h);
       if (rc) return rc;
     }
     void* args[] = {&P, &T};
@@ -503,6 +517,28 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
     void* args[] = {&P};
     e = cudaLaunchKernelExC(&cfg, k.fn, args);
   }
+  if (e == cudaSuccess) chained = true;
+  if (e != cudaSuccess || !split) return status_of(e);
+  // the curves and thresholds of the images whose last band this was: one
+  // block each, started while the pass ends (it waits for the pass grid)
+  bool any = false;
+  for (int j = 0; j < P.n; ++j) any = any || P.img[j].y1 == P.img[j].H;
+  if (!any) return KOHLER_OK;
+  cudaLaunchConfig_t c2 = {};
+  c2.gridDim = dim3(P.n);
+  c2.blockDim = dim3(kEpiThreads);
+  c2.dynamicSmemBytes = epi;
+  c2.stream = stream;
+  c2.attrs = attr;
+  c2.numAttrs = 1;
+  if (epi > 48 * 1024) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+      cudaFuncSetAttribute((const void*)k_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    });
+  }
+  void* a2[] = {&P};
+  e = cudaLaunchKernelExC(&c2, (const void*)k_finish, a2);
   return status_of(e);
 }
 
@@ -520,6 +556,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
   const int hist_words = hist_words_for(dt, M);
   int rc = get_workspace(stream, chunk, hist_words, cand_stride, &ws);
   if (rc) return rc;
+  bool chained = kohler::overlap_allowed(stream);
   for (int c0 = 0; c0 < n; c0 += chunk) {
     const int cn = std::min(chunk, n - c0);
     LaunchParams base;
@@ -552,7 +589,7 @@ int run_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, i
     if (bands) sub_bands.assign(bands->begin() + c0, bands->begin() + c0 + cn);
     for (auto& g : groups) {
       rc = launch_group(g.first, g.second, imgs + c0, bands ? &sub_bands : nullptr, M, bins, ws, base, stream, slot_of,
-                        out_index ? out_index + c0 : nullptr, force);
+                        out_index ? out_index + c0 : nullptr, chained, force);
       if (rc) return rc;
     }
   }
@@ -573,6 +610,36 @@ int validate_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t
 }  // namespace
 
 namespace kohler {
+namespace {
+std::atomic<int> g_alloc_faults{0};  // pending injected allocation failures
+std::atomic<int> g_wait_faults{0};   // pending injected ring-wait failures
+std::mutex g_overlap_mu;
+std::set<std::pair<int, uintptr_t>> g_overlap;  // (device, stream) pairs allowed to overlap
+bool take_one(std::atomic<int>& n) {
+  int v = n.load();
+  while (v > 0)
+    if (n.compare_exchange_weak(v, v - 1)) return true;
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (take_one(g_alloc_faults)) return cudaErrorMemoryAllocation;
+  return cudaMalloc(p, bytes);
+}
+cudaError_t host_malloc(void** p, size_t bytes) {
+  if (take_one(g_alloc_faults)) return cudaErrorMemoryAllocation;
+  return cudaHostAlloc(p, bytes, cudaHostAllocDefault);
+}
+bool take_wait_fault() { return take_one(g_wait_faults); }
+
+bool overlap_allowed(cudaStream_t stream) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lock(g_overlap_mu);
+  return g_overlap.count(std::make_pair(dev, (uintptr_t)stream)) != 0;
+}
+
 const char* pass_name(int pass) { return pass >= 0 && pass < kNumPasses ? kPassNames[pass] : "?"; }
 
 int pass_from_name(const char* name) {
@@ -708,7 +775,7 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
   const size_t cm = (size_t)n * M;
   void* dmem = nullptr;
   const size_t bytes = cm * 8 * 3 + (size_t)n * max_k * 4 + (size_t)n * 8;
-  e = cudaMalloc(&dmem, bytes);
+  e = kohler::dev_malloc(&dmem, bytes);
   if (e != cudaSuccess) {
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
@@ -860,6 +927,25 @@ int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int
   return KOHLER_OK;
 }
 
+int kohler_stream_overlap(void* cuda_stream, int32_t enable) {
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return status_of(e);
+  std::lock_guard<std::mutex> lock(kohler::g_overlap_mu);
+  const auto key = std::make_pair(dev, (uintptr_t)cuda_stream);
+  if (enable) kohler::g_overlap.insert(key);
+  else kohler::g_overlap.erase(key);
+  return KOHLER_OK;
+}
+
+int kohler_test_inject(int32_t kind, int32_t count) {
+  if (count < 0) return KOHLER_ERR_ARG;
+  if (kind == KOHLER_FAULT_ALLOC) kohler::g_alloc_faults.store(count);
+  else if (kind == KOHLER_FAULT_RING_WAIT) kohler::g_wait_faults.store(count);
+  else return KOHLER_ERR_ARG;
+  return KOHLER_OK;
+}
+
 int kohler_stream_status(void* cuda_stream) {
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   cudaError_t e = cudaStreamSynchronize(stream);
@@ -950,7 +1036,10 @@ void release_host_path(int dev) {
   if (h->dout) cudaFree(h->dout);
   if (h->hout) cudaFreeHost(h->hout);
   for (cudaEvent_t x : h->ev) cudaEventDestroy(x);
-  if (h->compute) cudaStreamDestroy(h->compute);
+  if (h->compute) {
+    kohler_stream_overlap(h->compute, 0);
+    cudaStreamDestroy(h->compute);
+  }
   if (h->copy) cudaStreamDestroy(h->copy);
   delete h;
   g_host.erase(it);
@@ -966,12 +1055,13 @@ int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
     h->device = dev;
     if ((e = cudaStreamCreateWithFlags(&h->compute, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
     if ((e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
+    kohler_stream_overlap(h->compute, 1);  // only this path's own launches, copies and waits
   }
   if (h->dimg_bytes < img_bytes) {
     if (h->dimg) cudaFree(h->dimg);
     h->dimg = nullptr;
     h->dimg_bytes = 0;
-    if ((e = cudaMalloc(&h->dimg, img_bytes + 64)) != cudaSuccess) return status_of(e);
+    if ((e = kohler::dev_malloc(&h->dimg, img_bytes + 64)) != cudaSuccess) return status_of(e);
     h->dimg_bytes = img_bytes;
   }
   if (h->dout_bytes < out_bytes) {
@@ -979,8 +1069,8 @@ int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
     if (h->hout) cudaFreeHost(h->hout);
     h->dout = h->hout = nullptr;
     h->dout_bytes = 0;
-    if ((e = cudaMalloc(&h->dout, out_bytes)) != cudaSuccess) return status_of(e);
-    if ((e = cudaHostAlloc(&h->hout, out_bytes, cudaHostAllocDefault)) != cudaSuccess) return status_of(e);
+    if ((e = kohler::dev_malloc(&h->dout, out_bytes)) != cudaSuccess) return status_of(e);
+    if ((e = kohler::host_malloc(&h->hout, out_bytes)) != cudaSuccess) return status_of(e);
     h->dout_bytes = out_bytes;
   }
   while ((int)h->ev.size() < bands) {
@@ -1178,5 +1268,8 @@ extern "C" int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t 
   base.cand = reinterpret_cast<int32_t*>(s + kCandAt);
   base.cand_stride = cand_ints(M);
   std::vector<int> idx(1, 0), slot_of(1, 0);
-  return launch_group(pass, idx, &im, nullptr, M, bins, nullptr, base, stream, slot_of, nullptr);
+  // the pass follows this call's own clearing of the array: it may overlap it
+  // (the clearing writes no image)
+  bool chained = true;
+  return launch_group(pass, idx, &im, nullptr, M, bins, nullptr, base, stream, slot_of, nullptr, chained);
 }

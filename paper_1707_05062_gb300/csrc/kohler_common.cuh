@@ -79,6 +79,7 @@ struct LaunchParams {
   int32_t* cand;              // [slot][cand_stride] threshold candidates scratch
   int32_t cand_stride;
   int32_t smem_bytes;         // dynamic shared memory of the launch (reused by the epilogue)
+  uint32_t fail_wait;         // test hook: nonzero makes the strip pass treat one completed ring wait as failed
   ImgDesc img[kMaxBatch];
 };
 
@@ -476,7 +477,9 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   const int M = P.M, bins = P.bins;
   unsigned long long* h = P.hist + (size_t)d.slot * P.hist_stride;
   __threadfence();
-  const bool bad = (__ldcg(P.err + d.slot) & kErrRange) != 0;
+  // a pixel >= M, or a ring wait of the strip pass that gave up: outputs zero
+  const unsigned ebits = __ldcg(P.err + d.slot);
+  const bool bad = ebits != 0u;
   uint64_t* card = P.card + (size_t)d.out * M;
   uint64_t* sumc = P.sumc + (size_t)d.out * M;
   double* curve = P.curve ? P.curve + (size_t)d.out * M : nullptr;
@@ -570,8 +573,9 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
                         P.out_t0 ? P.out_t0 + d.out : nullptr, cand, sh_int, scratch);
   }
   if (threadIdx.x == 0) {
-    if (P.out_status) P.out_status[d.out] = bad ? -3 : 0;  // KOHLER_ERR_RANGE / KOHLER_OK
-    if (bad) atomicOr(P.sticky, kErrRange);
+    // KOHLER_ERR_CUDA / KOHLER_ERR_RANGE / KOHLER_OK
+    if (P.out_status) P.out_status[d.out] = (ebits & kErrInternal) ? -5 : ((ebits & kErrRange) ? -3 : 0);
+    if (ebits) atomicOr(P.sticky, ebits & (kErrRange | kErrInternal));
     P.err[d.slot] = 0u;
     P.done[d.slot] = 0u;
   }

@@ -31,6 +31,18 @@ int stream_sticky(cudaStream_t stream, unsigned** sticky);
 // Frees the segmentation scratch of every stream of device `dev`.
 void release_segment(int dev);
 
+// Every device and pinned-host allocation of the library goes through these.
+// While an injected allocation failure is pending (kohler_test_inject), they
+// fail with cudaErrorMemoryAllocation and allocate nothing.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t host_malloc(void** p, size_t bytes);
+// Test hook: true (once per pending injection) if the next strip-pass launch
+// should treat one completed ring wait as failed.
+bool take_wait_fault();
+// Whether the caller allowed the library's first kernel of a call on `stream`
+// to overlap the stream's previous kernel (kohler_stream_overlap).
+bool overlap_allowed(cudaStream_t stream);
+
 // ----------------------------------------------------------------- autotuning
 // Launch parameters of one group of images that take the same pass.
 struct TuneVal {

@@ -379,7 +379,7 @@ int seg_workspace(cudaStream_t stream, int M, bool copies, SegWorkspace** out) {
   const size_t b_part = copies ? up256((size_t)kSegCopies * M * 8) : 0;
   const size_t total = b_cnt + b_cls + b_lut + 256 + b_part;
   void* mem = nullptr;
-  e = cudaMalloc(&mem, total);
+  e = kohler::dev_malloc(&mem, total);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KOHLER_ERR_NOMEM : KOHLER_ERR_CUDA;
   if (cudaMemsetAsync(mem, 0, total, stream) != cudaSuccess) {
     cudaFree(mem);

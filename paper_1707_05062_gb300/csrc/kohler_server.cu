@@ -146,7 +146,7 @@ void* kohler_server::dev_alloc(size_t bytes) {
   }
   if (dev_held + bytes > budget) return nullptr;
   void* p = nullptr;
-  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  if (kohler::dev_malloc(&p, bytes) != cudaSuccess) return nullptr;
   dev_held += bytes;
   return p;
 }
@@ -166,7 +166,7 @@ void* kohler_server::host_alloc(size_t bytes) {
   }
   if (host_held + bytes > staging_cap) return nullptr;
   void* p = nullptr;
-  if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) return nullptr;
+  if (kohler::host_malloc(&p, bytes) != cudaSuccess) return nullptr;
   host_held += bytes;
   return p;
 }
@@ -271,7 +271,8 @@ void kohler_server::retire(LaunchRec& L) {
     const int s = f->slot;
     f->t0 = h_t0[s];
     f->count = h_cnt[s];
-    f->status = h_status[s] == KOHLER_ERR_RANGE ? KOHLER_ERR_RANGE : KOHLER_OK;
+    // the launch's per-frame status: a pixel >= M, or a ring wait that gave up
+    f->status = (h_status[s] == KOHLER_ERR_RANGE || h_status[s] == KOHLER_ERR_CUDA) ? h_status[s] : KOHLER_OK;
     if (max_k > 0) f->ts.assign(h_t + (size_t)s * max_k, h_t + (size_t)(s + 1) * max_k);
     f->latency_s = std::chrono::duration<double>(now - f->t_submit).count();
     f->state = FrameState::Done;
@@ -377,21 +378,24 @@ int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t d
   chk(cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking));
   chk(cudaStreamCreateWithFlags(&s->direct, cudaStreamNonBlocking));
   chk(cudaEventCreateWithFlags(&s->direct_done, cudaEventDisableTiming));
-  chk(cudaMalloc(&s->d_card, sizeof(uint64_t) * M * n));
-  chk(cudaMalloc(&s->d_sumc, sizeof(uint64_t) * M * n));
-  chk(cudaMalloc(&s->d_curve, sizeof(double) * M * n));
-  chk(cudaMalloc(&s->d_t, sizeof(int32_t) * std::max(max_k, 1) * n));
-  chk(cudaMalloc(&s->d_cnt, sizeof(int32_t) * n));
-  chk(cudaMalloc(&s->d_t0, sizeof(int32_t) * n));
-  chk(cudaMalloc(&s->d_status, sizeof(int32_t) * n));
-  chk(cudaHostAlloc(&s->h_t, sizeof(int32_t) * std::max(max_k, 1) * n, cudaHostAllocDefault));
-  chk(cudaHostAlloc(&s->h_cnt, sizeof(int32_t) * n, cudaHostAllocDefault));
-  chk(cudaHostAlloc(&s->h_t0, sizeof(int32_t) * n, cudaHostAllocDefault));
-  chk(cudaHostAlloc(&s->h_status, sizeof(int32_t) * n, cudaHostAllocDefault));
+  chk(kohler::dev_malloc((void**)&s->d_card, sizeof(uint64_t) * M * n));
+  chk(kohler::dev_malloc((void**)&s->d_sumc, sizeof(uint64_t) * M * n));
+  chk(kohler::dev_malloc((void**)&s->d_curve, sizeof(double) * M * n));
+  chk(kohler::dev_malloc((void**)&s->d_t, sizeof(int32_t) * std::max(max_k, 1) * n));
+  chk(kohler::dev_malloc((void**)&s->d_cnt, sizeof(int32_t) * n));
+  chk(kohler::dev_malloc((void**)&s->d_t0, sizeof(int32_t) * n));
+  chk(kohler::dev_malloc((void**)&s->d_status, sizeof(int32_t) * n));
+  chk(kohler::host_malloc((void**)&s->h_t, sizeof(int32_t) * std::max(max_k, 1) * n));
+  chk(kohler::host_malloc((void**)&s->h_cnt, sizeof(int32_t) * n));
+  chk(kohler::host_malloc((void**)&s->h_t0, sizeof(int32_t) * n));
+  chk(kohler::host_malloc((void**)&s->h_status, sizeof(int32_t) * n));
   if (e != cudaSuccess) {
     kohler_server_destroy(s);
     return status_of(e);
   }
+  // the compute stream holds only the server's own launches, copies and
+  // event waits: each launch may overlap the previous one's end
+  kohler_stream_overlap(s->compute, 1);
   for (int i = n - 1; i >= 0; --i) s->free_slots.push_back(i);
   s->worker = std::thread([s] { s->run(); });
   *out = s;
@@ -638,7 +642,10 @@ int kohler_server_destroy(kohler_server* s) {
   cudaFreeHost(s->h_status);
   if (s->direct) cudaStreamSynchronize(s->direct);
   if (s->copy) cudaStreamDestroy(s->copy);
-  if (s->compute) cudaStreamDestroy(s->compute);
+  if (s->compute) {
+    kohler_stream_overlap(s->compute, 0);
+    cudaStreamDestroy(s->compute);
+  }
   if (s->direct) cudaStreamDestroy(s->direct);
   if (s->direct_done) cudaEventDestroy(s->direct_done);
   delete s;

@@ -246,7 +246,13 @@ __device__ __forceinline__ void u8h_group(uint32_t ra, uint32_t K, bool act, boo
   if (FULL || act) u8h_row<CHECK>(Pn, Pc, mU, D0, Dm, D7, C, vmax);
 }
 
-template <bool CHECK, int NMAP>
+// SPLIT: the curves and thresholds come from k_finish, launched right after
+// this grid (no completion counting here); else the block that completes an
+// image runs its epilogue.  A ring wait that gives up marks the image (outputs
+// zero, status KOHLER_ERR_CUDA) and the stream; the warp then issues no
+// further copy and waits, with a bound, for those in flight before the block
+// folds and exits.
+template <bool CHECK, int NMAP, bool SPLIT>
 __global__ void __launch_bounds__(u8h::kNW * 32, 1)
     k_u8h(const __grid_constant__ LaunchParams P, const __grid_constant__ ImgMaps<NMAP> T) {
   using namespace u8h;
@@ -274,6 +280,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   rg.cur = 0u;
   rg.rin = 0;
   rg.failed = false;
+  uint32_t issued = 0, waited = 0;  // copies of this warp issued and waited for
+  const bool inject = P.fail_wait != 0u && blockIdx.x == 0 && warp == 0;
   if (lane == 0)
     for (int s = 0; s < kSlots; ++s) mbar_init(rg.bar0 + 8u * s, 1u);
   if (threadIdx.x == 0) sh_rows = 0u;
@@ -303,6 +311,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
     const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * units_col);
     const int W = d.W, H = d.H;
     uint32_t vmax = 0;
+    bool img_failed = false;
     for (int64_t base = r0; base < seg_end; base += (int64_t)kNW * kRowsPerRound) {
       const int n_r = (int)min64((int64_t)kNW * kRowsPerRound, seg_end - base);
       uint32_t a = (uint32_t)(base - d.rs_begin) + (uint32_t)((n_r * warp) / kNW);
@@ -330,18 +339,26 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         }
         const uint32_t slot = rg.islot;
         rg.islot = slot == kSlots - 1 ? 0u : slot + 1u;
-        if (lane == 0) {
-          const uint32_t bar = rg.bar0 + 8u * slot;
-          fence_proxy_async();
-          mbar_expect_tx(bar, kBoxBytes);
-          tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_y0 + p_gi * kGroupRows, bar);
+        if (!rg.failed) {
+          if (lane == 0) {
+            const uint32_t bar = rg.bar0 + 8u * slot;
+            fence_proxy_async();
+            mbar_expect_tx(bar, kBoxBytes);
+            tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_y0 + p_gi * kGroupRows, bar);
+          }
+          ++issued;
         }
         ++p_gi;
       };
       for (int k = 0; k < kSlots; ++k) produce();
       auto wait_group = [&]() {
-        if (!mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase)) rg.failed = true;
         rg.cur = rg.ring0 + rg.wslot * kSlotBytes + 8u * (uint32_t)lane;
+        if (rg.failed) return;  // no data to wait for: the image's results are discarded
+        if (!mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase) || (inject && waited == 0)) {
+          rg.failed = true;
+          if (!inject || waited != 0) return;  // the copy may still be in flight: drained below
+        }
+        ++waited;
         rg.wphase ^= rg.wslot == kSlots - 1 ? 1u : 0u;
         rg.wslot = rg.wslot == kSlots - 1 ? 0u : rg.wslot + 1u;
       };
@@ -432,24 +449,57 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         while (y < yb) row_any(y++);
       }
       if (lane == 0 && rows_done) atomicAdd(&sh_rows, rows_done);
+      if (rg.failed) img_failed = true;
+      // copies in flight after a failed wait: wait for them (bounded) before
+      // the ring's memory is reused or the block exits
+      while (rg.failed && waited < issued) {
+        mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase);
+        ++waited;
+        rg.wphase ^= rg.wslot == kSlots - 1 ? 1u : 0u;
+        rg.wslot = rg.wslot == kSlots - 1 ? 0u : rg.wslot + 1u;
+      }
       wait_prior();
       __syncthreads();
-      u8h_fold_flush(P, i, region, xch, base + (int64_t)kNW * kRowsPerRound < seg_end);
+      // with SPLIT, the last fold of an image also clears the bins when the
+      // block goes on to another image
+      u8h_fold_flush(P, i, region, xch,
+                     base + (int64_t)kNW * kRowsPerRound < seg_end || (SPLIT && seg_end < r1));
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
-    if (rg.failed) atomicOr(P.sticky, kErrInternal);
-    const unsigned rows = sh_rows;  // strip-rows of image i reduced by this block
-    image_rows_done(P, i, rows, scratch, sh_int, reinterpret_cast<unsigned char*>(region), (size_t)kRegionBytes);
-    if (threadIdx.x == 0) sh_rows = 0u;
+    if (img_failed && lane == 0) {
+      atomicOr(P.err + d.slot, kErrInternal);
+      atomicOr(P.sticky, kErrInternal);
+    }
+    if (!SPLIT) {
+      const unsigned rows = sh_rows;  // strip-rows of image i reduced by this block
+      image_rows_done(P, i, rows, scratch, sh_int, reinterpret_cast<unsigned char*>(region), (size_t)kRegionBytes);
+      if (threadIdx.x == 0) sh_rows = 0u;
+    }
     r0 = seg_end;
     ++i;
-    if (r0 < r1) {  // the epilogue may have used the region as scratch
+    if (!SPLIT && r0 < r1) {  // the epilogue may have used the region as scratch
       uint4* r4 = reinterpret_cast<uint4*>(region);
       for (int k = threadIdx.x; k < (int)(kRegionBytes / 16); k += blockDim.x) r4[k] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
   }
+}
+
+// Curves and thresholds of the images of a split strip-pass launch, one block
+// per image (launched right after the pass, programmatic dependent launch):
+// waits for the pass grid, then the shared epilogue.  Images whose band ends
+// above the image's last row (an earlier band of a banded launch) are left for
+// the launch of their last band.
+__global__ void __launch_bounds__(kEpiThreads, 1) k_finish(const __grid_constant__ LaunchParams P) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ uint64_t scratch[kScratch];
+  __shared__ int sh_int[kShInts];
+  allow_dependents();
+  wait_prior();
+  const int i = blockIdx.x;
+  if (i >= P.n || P.img[i].y1 != P.img[i].H) return;
+  finish_image(P, i, scratch, sh_int, dsm, (size_t)P.smem_bytes);
 }
 
 }  // namespace kohler

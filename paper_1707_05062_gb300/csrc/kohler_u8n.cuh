@@ -324,7 +324,10 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
-    if (rg.failed) atomicOr(P.sticky, kErrInternal);
+    if (rg.failed) {
+      atomicOr(P.err + d.slot, kErrInternal);  // the image's outputs become zero, its status KOHLER_ERR_CUDA
+      atomicOr(P.sticky, kErrInternal);
+    }
     const unsigned rows = sh_rows;
     image_rows_done(P, i, rows, scratch, sh_int, reinterpret_cast<unsigned char*>(region), (size_t)kRegionBytes);
     if (threadIdx.x == 0) sh_rows = 0u;
