@@ -265,22 +265,25 @@ def bench_ours(args, rank, local, world, dist):
                       and np.array_equal(sumc[0].cpu().numpy().view(np.uint64), osumc)
                       and np.array_equal(c[0].cpu().numpy(), oc) and np.array_equal(ts[0].cpu().numpy(), ots)
                       and int(cnt[0]) == ocnt and int(t0[0]) == ot0)
-    # The K steps run as replays of CUDA graphs of the fused launch (48 launches
-    # per graph, the pool cycled inside; a second graph holds the remainder), so
-    # the host's per-call cost does not pace the GPU.  One event pair spans all
-    # replays: events between launches would stop a launch from overlapping the
-    # previous one's epilogue (programmatic launch).
-    G = 48
+    # The K steps are one CUDA graph of K fused launches (the pool cycled
+    # inside; at most 512 launches per graph, several graphs for larger K), so
+    # the host's per-call cost does not pace the GPU.  The graph is replayed R
+    # times; each replay is one timed block of exactly K steps between a
+    # barrier and a synchronize on both sides, timed by an event pair on the
+    # launching stream (events inside a block would stop a launch from
+    # overlapping the previous one's epilogue).  ms_per_step is the median
+    # block over K; p90 is reported beside it.
     gstream = torch.cuda.Stream(dev)
     # every kernel before a call on these streams is the library's own previous
     # call: let each call's pass overlap the previous call's epilogue
     K.stream_overlap(gstream)
     K.stream_overlap(stream)
+    G = 512
 
-    def capture(n):
+    def capture(j0, n):
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=gstream):
-            for j in range(n):
+            for j in range(j0, j0 + n):
                 K.analyze_batch([pool[j % POOL]], M, MAX_K, out=outs, stream=gstream)
         return g
 
@@ -288,28 +291,35 @@ def bench_ours(args, rank, local, world, dist):
         for i in range(3):  # creates the library's workspace for this stream before capture
             K.analyze_batch([pool[i % POOL]], M, MAX_K, out=outs, stream=gstream)
     torch.cuda.synchronize(dev)
-    g_full = capture(G)
-    g_rest = capture(args.steps % G) if args.steps % G else None
-    with torch.cuda.stream(gstream):
-        for _ in range(max(1, args.warmup // G)):
-            g_full.replay()
+    graphs = [capture(j0, min(G, args.steps - j0)) for j0 in range(0, args.steps, G)]
+
+    def replay_all():
+        with torch.cuda.stream(gstream):
+            for g in graphs:
+                g.replay()
+
+    replay_all()  # warm replay
     torch.cuda.synchronize(dev)
+    est_block_s = args.steps * 16e-6
+    # about one second of blocks, so that the clock samples (every 20 ms) cover them
+    R = args.reps if args.reps > 0 else int(max(5, min(2000, 1.0 / max(est_block_s, 1e-9))))
     sampler = ClockSampler(local)
     time.sleep(0.3)
-    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    blocks = []
     barrier(dist)
     torch.cuda.synchronize(dev)
     sampler.mark_start()
     t_start = time.perf_counter()
-    with torch.cuda.stream(gstream):
+    for _ in range(R):
+        barrier(dist)
+        torch.cuda.synchronize(dev)
+        e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e_start.record(gstream)
-        for _ in range(args.steps // G):
-            g_full.replay()
-        if g_rest is not None:
-            g_rest.replay()
+        replay_all()
         e_end.record(gstream)
-    torch.cuda.synchronize(dev)
-    barrier(dist)
+        torch.cuda.synchronize(dev)
+        barrier(dist)
+        blocks.append(e_start.elapsed_time(e_end) / 1e3)
     t_host = time.perf_counter() - t_start
     sampler.mark_end()
     time.sleep(0.1)
@@ -317,7 +327,8 @@ def bench_ours(args, rank, local, world, dist):
     st = K.stream_status(gstream)
     if st != K.OK:
         raise RuntimeError(f"timed run reported status {st}")
-    dev_s = e_start.elapsed_time(e_end) / 1e3
+    dev_s = float(np.median(blocks))
+    dev_p90 = float(np.percentile(blocks, 90))
     # the same steps launched one by one from Python through the binding, for reference
     outt = outs
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -337,11 +348,11 @@ def bench_ours(args, rank, local, world, dist):
         b.record(stream)
         b.synchronize()
         launch_ms.append(a.elapsed_time(b))
-    elapsed = max_over_ranks(dist, dev_s)
+    elapsed = max_over_ranks(dist, dev_s)  # one block of K steps: the median over the R blocks
     host_elapsed = max_over_ranks(dist, t_host)
     total_px = sum_over_ranks(dist, float(px * args.steps))
     value = total_px / elapsed / 1e9
-    mean_launch_s = dev_s / args.steps  # one launch per step, back to back
+    mean_launch_s = dev_s / args.steps  # one fused launch (pass + epilogue kernel) per step, back to back
     peak, peak_src = measured_peak_hbm()
     achieved = px / mean_launch_s / 1e9  # algorithmic bytes: one read of each 1-byte pixel
     traffic = kernel_traffic("k_u8h", "voronoi_18mp")
@@ -357,10 +368,14 @@ def bench_ours(args, rank, local, world, dist):
         "config": {"workload": "voronoi_18mp", "image": f"{W}x{H} uint8", "M": M, "max_k": MAX_K,
                    "images_per_step": 1, "per_gpu_pool": f"{POOL} distinct images ({POOL * px / 1e6:.0f} MB) cycled",
                    "l2": "inputs larger than L2 (rotating pool), no flush", "parallelism": f"replicas x{world}",
-                   "launch": "CUDA-graph replays, 48 fused launches per graph"},
+                   "launch": f"one CUDA graph of the K fused launches, replayed R = {R} times",
+                   "timing": {"blocks_R": R, "steps_per_block": args.steps,
+                              "block_ms_median": dev_s * 1e3, "block_ms_p90": dev_p90 * 1e3,
+                              "ms_per_step_p90": dev_p90 * 1e3 / args.steps,
+                              "statistic": "median block / K (p90 beside it); max over ranks"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"hbm_gbs of {peak_src}",
-                     "kernel": "k_u8h (fused pass + epilogue + thresholds)",
+                     "kernel": "k_u8h (strip pass) + k_finish (curve, thresholds), one step",
                      "mean_launch_us": mean_launch_s * 1e6,
                      "isolated_launch_p50_us": float(np.median(launch_ms)) * 1e3,
                      "host_launched_us_per_step": host_launched_us},
@@ -373,6 +388,7 @@ def bench_ours(args, rank, local, world, dist):
         line["cpu_baseline"] = cpu
     if forms is not None:
         line["forms"] = forms
+        line["forms_summary"] = forms_summary(forms)  # last key: stays in a tail of the output
     return line
 
 
@@ -857,6 +873,145 @@ def form_nbhd(K, torch, dev, peak, n_pool=6):
     return out
 
 
+def form_ceiling(K, torch, dev, peak):
+    """Microbenchmarks of the ceilings the strip pass runs into (libkohler_probe):
+    conflict-free shared-memory additions and three-input integer additions per
+    clock per SM, and the per-row work of the four-addition (k_u8h) and the
+    three-addition formulations on register data, in pixels per clock per SM,
+    with the rates they imply on this GPU."""
+    import ctypes
+
+    from paper_1707_05062_gb300 import build as kbuild
+
+    L = ctypes.CDLL(kbuild.PROBE_LIB)
+    L.kohler_probe_run.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p]
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    cyc = torch.zeros(sms, dtype=torch.int64, device=dev)
+    sink = torch.zeros(1024, dtype=torch.int32, device=dev)
+    s = torch.cuda.current_stream(dev)
+    out = {"sms": sms, "warps_per_sm": 16}
+
+    def run(which, iters):
+        for _ in range(2):
+            a, b = _events(torch)
+            a.record(s)
+            if L.kohler_probe_run(which, sms, iters, cyc.data_ptr(), sink.data_ptr(), ctypes.c_void_p(s.cuda_stream)):
+                raise RuntimeError("probe launch failed")
+            b.record(s)
+            b.synchronize()
+        c = cyc.cpu().numpy().astype(np.float64)
+        return float(np.median(c)), a.elapsed_time(b) / 1e3
+
+    cyc_red, t_red = run(0, 4000)
+    out["shared_add_warp_inst_per_clk_sm"] = 16 * 4000 * 16 / cyc_red
+    cyc_add, _ = run(1, 4000)
+    out["int_add3_warp_inst_per_clk_sm"] = 16 * 4000 * 32 / cyc_add
+    mhz = cyc_red / t_red / 1e6  # clock seen by the probe (cycles of the median block over the launch time)
+    out["sm_mhz_during_probe"] = mhz
+    for which, name, upd in ((2, "rows_4_additions", 4), (3, "rows_3_additions", 3)):
+        c, _ = run(which, 200)
+        ppc = 16 * 200 * 4 * 256 / c
+        gpx = ppc * sms * mhz * 1e6 / 1e9
+        out[name] = {"px_per_clk_sm": ppc, "implied_gpx_s": gpx, "implied_hbm_frac_u8": gpx / peak,
+                     "shared_add_bound_px_per_clk_sm": out["shared_add_warp_inst_per_clk_sm"] * 32 / upd}
+    out["reading"] = ("the per-row work alone runs at the shared-add bound for 4 additions per pixel; the strip "
+                      "pass adds the ring's tensor-copy writes and row loads to the same shared-memory pipe "
+                      "(profiles/k_u8h_voronoi_18mp.md) and pays fixed per-launch phases")
+    return out
+
+
+def form_blobs(K, torch, dev, reps=300):
+    """Config 1: one 256 x 256 uint8 blobs image, M = 256, the plain single-image
+    path.  Launch-bound, so reported as latency: one call as a CUDA-graph replay
+    (device events around each replay), one call through the host-buffer entry
+    point (host wall clock, copies included), and back-to-back graph throughput."""
+    import oracle
+    import synth
+
+    img_np = synth.blobs_image()
+    img = torch.from_numpy(img_np).to(dev)
+    outs = alloc_outputs(torch, dev, 1, 256)
+    g1, s1 = _graph_of(torch, dev, lambda s: K.analyze_batch([img], 256, MAX_K, out=outs, stream=s))
+    lat = []
+    for _ in range(reps):
+        a, b = _events(torch)
+        with torch.cuda.stream(s1):
+            a.record(s1)
+            g1.replay()
+            b.record(s1)
+        b.synchronize()
+        lat.append(a.elapsed_time(b) * 1e3)
+    n = 100
+    gN, sN = _graph_of(torch, dev, lambda s: [K.analyze_batch([img], 256, MAX_K, out=outs, stream=s) for _ in range(n)])
+    t_n = _time_graph(torch, gN, sN, 5)
+    pinned = torch.from_numpy(img_np).pin_memory()
+    hout = K.host_outputs(256, MAX_K)
+    for _ in range(5):
+        K.analyze_host(pinned, 256, MAX_K, out=hout)
+    hl = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        K.analyze_host(pinned, 256, MAX_K, out=hout)
+        hl.append((time.perf_counter() - t) * 1e6)
+    if K.stream_status(s1) != K.OK or K.stream_status(sN) != K.OK:
+        raise RuntimeError("blobs_256: a launch reported an error")
+    ocard, osumc, oc, ots, ocnt, ot0 = oracle.analyze(img_np, 256, MAX_K, method="def")
+    ok = bool(np.array_equal(outs[0][0].cpu().numpy().view(np.uint64), ocard)
+              and np.array_equal(outs[1][0].cpu().numpy().view(np.uint64), osumc)
+              and np.array_equal(outs[2][0].cpu().numpy(), oc) and np.array_equal(outs[3][0].cpu().numpy(), ots))
+    return {"workload": "256x256 uint8 blobs image, M = 256, plain single-image path",
+            "graph_call_us_p50": _pct(lat, 50), "graph_call_us_p99": _pct(lat, 99),
+            "host_call_us_p50": _pct(hl, 50), "host_call_us_p99": _pct(hl, 99),
+            "back_to_back_us_per_image": t_n * 1e6 / n, "back_to_back_gpx_s": img_np.size * n / t_n / 1e9,
+            "host_call": "kohler_analyze_host: pinned image in, curve and thresholds out", "calls": reps,
+            "parity_spot_check": ok}
+
+
+def forms_summary(forms):
+    """The forms' headline numbers in a few hundred bytes."""
+    out = {}
+
+    def g(d, *ks):
+        for k in ks:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return round(d, 4) if isinstance(d, float) else d
+
+    for name, f in forms.items():
+        if not isinstance(f, dict) or "error" in f:
+            out[name] = {"error": (f or {}).get("error") if isinstance(f, dict) else "?"}
+            continue
+        if name in ("batch96", "cosine_u16_batch16"):
+            out[name] = {"batched_ms": g(f, "batched", "ms_graph"), "batched_gpx_s": g(f, "batched", "gpx_s_graph"),
+                         "batched_hbm_frac": g(f, "batched", "hbm_frac_graph"), "plain_ms": g(f, "plain", "ms_graph"),
+                         "batched_over_plain": g(f, "batched_over_plain_graph"), "tuned_ms": g(f, "tuned", "ms_graph"),
+                         "tuned_hbm_frac": g(f, "tuned", "hbm_frac_graph"),
+                         "parity": g(f, "parity_spot_check", "equal")}
+        elif name == "served":
+            out[name] = {"open_p50_ms": g(f, "open_loop", "latency_ms_p50"), "open_p99_ms": g(f, "open_loop", "latency_ms_p99"),
+                         "open_max_frames_per_launch": g(f, "open_loop", "max_frames_per_launch"),
+                         "closed_fps": g(f, "closed_loop", "fps"), "closed_gpx_s": g(f, "closed_loop", "gpx_s"),
+                         "closed_max_frames_per_launch": g(f, "closed_loop", "max_frames_per_launch"),
+                         "plain_fps": g(f, "plain_per_frame", "fps"),
+                         "seg_p99_ms": g(f, "segmented_open_loop", "latency_ms_p99"), "parity": f.get("parity_all_frames")}
+        elif name == "segment":
+            out[name] = {"ms": g(f, "segment_ms"), "hbm_frac": g(f, "segment_hbm_frac"), "parity": f.get("parity_spot_check")}
+        elif name == "nbhd":
+            out[name] = {k: {"ms": g(f, k, "ms"), "hbm_frac": g(f, k, "hbm_frac")} for k in ("N4", "N8", "N6")}
+        elif name == "ceiling":
+            out[name] = {"shared_add_per_clk_sm": g(f, "shared_add_warp_inst_per_clk_sm"),
+                         "rows4_px_per_clk_sm": g(f, "rows_4_additions", "px_per_clk_sm"),
+                         "rows4_hbm_frac": g(f, "rows_4_additions", "implied_hbm_frac_u8"),
+                         "rows3_px_per_clk_sm": g(f, "rows_3_additions", "px_per_clk_sm")}
+        elif name == "blobs_256":
+            out[name] = {"graph_us_p50": g(f, "graph_call_us_p50"), "graph_us_p99": g(f, "graph_call_us_p99"),
+                         "host_us_p50": g(f, "host_call_us_p50"), "host_us_p99": g(f, "host_call_us_p99"),
+                         "parity": f.get("parity_spot_check")}
+    return out
+
+
 def run_forms(args, K, torch, dev, peak):
     forms = {}
     names = [x for x in args.forms.split(",") if x]
@@ -885,6 +1040,10 @@ def run_forms(args, K, torch, dev, peak):
                 forms[name] = form_segment(K, torch, dev, peak)
             elif name == "nbhd":
                 forms[name] = form_nbhd(K, torch, dev, peak)
+            elif name == "ceiling":
+                forms[name] = form_ceiling(K, torch, dev, peak)
+            elif name == "blobs_256":
+                forms[name] = form_blobs(K, torch, dev)
             else:
                 forms[name] = {"error": "unknown form"}
         except Exception as e:  # a failing form is reported, not hidden
@@ -983,7 +1142,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
-    ap.add_argument("--forms", default="batch96,cosine_u16_batch16,served,segment,nbhd",
+    ap.add_argument("--reps", type=int, default=0, help="timed blocks of K steps (0: about 1 s of blocks, 5..2000)")
+    ap.add_argument("--forms", default="ceiling,blobs_256,batch96,cosine_u16_batch16,served,segment,nbhd",
                     help="comma list of extra forms reported in the same line (N = 1 only); empty for none")
     ap.add_argument("--ncu-case", choices=NCU_CASES, default=None,
                     help="run only a small fixed workload of one kernel (for ncu captures) and exit")
