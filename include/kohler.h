@@ -263,7 +263,8 @@ int32_t kohler_tune_count(void);
  * continuous batching (the video use of Section 4, Table 2): a host thread
  * admits submitted frames into device slots as slots and device memory free
  * up, copies them on a copy stream, and each launch reduces every frame that
- * is resident and copied at that moment; results are copied back per frame.
+ * is resident and copied at that moment; while two launches are on the GPU,
+ * ready frames wait and share the next one.  Results are copied back per frame.
  * Frames are uint8 or uint16 with the server's M. */
 typedef struct kohler_server kohler_server;
 
@@ -283,6 +284,11 @@ typedef struct {
  * Pinned staging for submitted frames is capped at 1 GiB. */
 int kohler_server_create(kohler_server** s, int32_t M, int32_t max_k, size_t device_mem_budget,
                          int32_t max_inflight);
+/* kohler_server_create with the pinned staging capped at staging_bytes (0 =
+ * 1 GiB): kohler_submit returns KOHLER_ERR_BUSY for a frame that must wait and
+ * whose copy would take the staging above the cap. */
+int kohler_server_create_ex(kohler_server** s, int32_t M, int32_t max_k, size_t device_mem_budget,
+                            int32_t max_inflight, size_t staging_bytes);
 
 /* Takes a copy of the frame (row-major, pitch_bytes) and queues it; the caller
  * may reuse `host_frame` as soon as the call returns.  When no earlier frame is
@@ -292,6 +298,18 @@ int kohler_server_create(kohler_server** s, int32_t M, int32_t max_k, size_t dev
  * identifies the frame.  KOHLER_ERR_BUSY when the staging queue is full. */
 int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                   int64_t pitch_bytes, uint64_t* ticket);
+
+/* kohler_submit without the copy into the call: the server reads `host_frame`
+ * asynchronously on its copy stream, so the call returns at once and several
+ * frames' copies can be in flight together; frames whose copies have finished
+ * by the time the GPU can take work share one launch (the paper has no
+ * counterpart: a serving choice).  The caller keeps `host_frame` allocated and
+ * unchanged until kohler_poll has returned for the ticket (any status); it
+ * should be pinned (a pageable buffer makes the copy synchronous).  Frames that
+ * cannot be admitted at once (no slot or device memory) wait in the queue
+ * without a staging copy.  Errors as kohler_submit (never KOHLER_ERR_BUSY). */
+int kohler_submit_borrowed(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                           int64_t pitch_bytes, uint64_t* ticket);
 
 /* kohler_submit that also returns the frame segmented into two classes by its
  * own optimal threshold t0 (Section 4: video frames segmented by the method into

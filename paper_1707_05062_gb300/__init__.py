@@ -88,13 +88,16 @@ def lib():
                 getattr(L, name).restype = i
             if hasattr(L, "kohler_server_create"):
                 L.kohler_server_create.argtypes = [p, i32, i32, ctypes.c_size_t, i32]
+                L.kohler_server_create_ex.argtypes = [p, i32, i32, ctypes.c_size_t, i32, ctypes.c_size_t]
                 L.kohler_submit.argtypes = [p, p, i, i64, i64, i64, p]
                 L.kohler_submit_segment.argtypes = [p, p, i, i64, i64, i64, p, i64, p]
+                L.kohler_submit_borrowed.argtypes = [p, p, i, i64, i64, i64, p]
                 L.kohler_poll.argtypes = [p, ctypes.c_uint64, p, i64]
                 L.kohler_server_curve.argtypes = [p, ctypes.c_uint64, p]
                 L.kohler_server_stats.argtypes = [p, p, p, p, p]
                 L.kohler_server_destroy.argtypes = [p]
-                for name in ("kohler_server_create", "kohler_submit", "kohler_submit_segment", "kohler_poll",
+                for name in ("kohler_server_create", "kohler_server_create_ex", "kohler_submit", "kohler_submit_segment", "kohler_submit_borrowed",
+                             "kohler_poll",
                              "kohler_server_curve",
                              "kohler_server_stats", "kohler_server_destroy"):
                     getattr(L, name).restype = i

@@ -45,6 +45,8 @@ struct Frame {
   std::vector<int32_t> ts;
   void* host_out = nullptr;  // kohler_submit_segment: the caller's buffer for the two-class frame
   int64_t out_pitch = 0;
+  const void* borrowed = nullptr;  // kohler_submit_borrowed: the caller's frame, read by the copy
+  int64_t src_pitch = 0;
 };
 
 struct LaunchRec {
@@ -93,6 +95,8 @@ struct kohler_server {
   uint64_t next_ticket = 1;
   uint64_t n_submitted = 0, n_finished = 0, n_launches = 0, max_per_launch = 0;
   int running = 0;  // frames in launched-but-unfinished state
+  int launches_active = 0;  // launches made and not yet retired
+  static constexpr int kMaxLaunchesActive = 2;  // more ready frames wait and share the next launch
   bool stop = false;
   int fatal = KOHLER_OK;
   std::thread worker;
@@ -175,6 +179,9 @@ void* kohler_server::host_alloc(size_t bytes) {
 // (up to 64), with the copies of its results to the pinned mirrors and a done
 // event.  Called with `mu` held, by the scheduler thread or by kohler_submit.
 bool kohler_server::launch_ready() {
+  // continuous batching: while two launches are on the GPU, frames whose copy
+  // has finished wait, and the next launch takes all of them
+  if (launches_active >= kMaxLaunchesActive) return false;
   std::vector<Frame*> ready;
   for (auto it = copying.begin(); it != copying.end() && ready.size() < 64;) {
     Frame* f = *it;
@@ -256,6 +263,7 @@ bool kohler_server::launch_ready() {
       }
       cv_done.notify_all();  // pollers of these frames now wait on the launch's event
       running += (int)fr.size();
+      ++launches_active;
       ++n_launches;
       max_per_launch = std::max<uint64_t>(max_per_launch, fr.size());
     }
@@ -285,6 +293,7 @@ void kohler_server::retire(LaunchRec& L) {
   L.done = nullptr;
   L.frames.clear();
   L.active = false;
+  --launches_active;
   cv_done.notify_all();
 }
 
@@ -319,8 +328,10 @@ void kohler_server::run() {
       f->slot = free_slots.back();
       free_slots.pop_back();
       const int es = f->dt == KOHLER_U8 ? 1 : 2;
-      cudaError_t e = cudaMemcpy2DAsync(d, f->dpitch, f->staging, f->W * es, f->W * es, f->H, cudaMemcpyHostToDevice,
-                                        copy);
+      cudaError_t e = f->borrowed ? cudaMemcpy2DAsync(d, f->dpitch, f->borrowed, f->src_pitch, f->W * es, f->H,
+                                                      cudaMemcpyHostToDevice, copy)
+                                  : cudaMemcpy2DAsync(d, f->dpitch, f->staging, f->W * es, f->W * es, f->H,
+                                                      cudaMemcpyHostToDevice, copy);
       f->copied = get_event();
       if (e == cudaSuccess && f->copied) e = cudaEventRecord(f->copied, copy);
       if (e != cudaSuccess || !f->copied) {
@@ -334,14 +345,14 @@ void kohler_server::run() {
       copying.push_back(f);
       progressed = true;
     }
-    // (2) one launch over the frames whose copies are complete
-    if (launch_ready()) progressed = true;
-    // (3) retire finished launches
+    // (2) retire finished launches
     for (auto& L : launches) {
       if (!L.active || cudaEventQuery(L.done) != cudaSuccess) continue;
       retire(L);
       progressed = true;
     }
+    // (3) one launch over the frames whose copies are complete
+    if (launch_ready()) progressed = true;
     const bool busy = !copying.empty() || running > 0;
     if (stop && !busy) break;  // admitted frames are drained, queued ones dropped
     if (progressed) continue;
@@ -352,7 +363,7 @@ void kohler_server::run() {
       lk.lock();
     } else {
       cv_work.wait(lk, [&] {
-        return stop || !copying.empty() || (!queue.empty() && !free_slots.empty());
+        return stop || !copying.empty() || running > 0 || (!queue.empty() && !free_slots.empty());
       });
     }
   }
@@ -360,14 +371,15 @@ void kohler_server::run() {
 
 extern "C" {
 
-int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t device_mem_budget,
-                         int32_t max_inflight) {
+int kohler_server_create_ex(kohler_server** out, int32_t M, int32_t max_k, size_t device_mem_budget,
+                            int32_t max_inflight, size_t staging_bytes) {
   if (!out || M < 2 || M > 65536 || max_k < 0 || max_inflight < 0) return KOHLER_ERR_ARG;
   kohler_server* s = new kohler_server();
   cudaGetDevice(&s->device);
   s->M = M;
   s->max_k = max_k;
   s->budget = device_mem_budget ? device_mem_budget : (1ull << 30);
+  s->staging_cap = staging_bytes ? staging_bytes : (1ull << 30);
   s->max_inflight = max_inflight ? max_inflight : 64;
   const int n = s->max_inflight;
   cudaError_t e = cudaSuccess;
@@ -402,13 +414,18 @@ int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t d
   return KOHLER_OK;
 }
 
+int kohler_server_create(kohler_server** out, int32_t M, int32_t max_k, size_t device_mem_budget,
+                         int32_t max_inflight) {
+  return kohler_server_create_ex(out, M, max_k, device_mem_budget, max_inflight, 0);
+}
+
 }  // extern "C"
 
 namespace {
 // kohler_submit and kohler_submit_segment (host_out non-null: the frame is
 // segmented at its t0 and copied back into host_out).
 int submit_frame(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
-                 int64_t pitch_bytes, void* host_out, int64_t out_pitch, uint64_t* ticket) {
+                 int64_t pitch_bytes, void* host_out, int64_t out_pitch, uint64_t* ticket, bool borrow = false) {
   if (!s || !host_frame || !ticket || (dt != KOHLER_U8 && dt != KOHLER_U16)) return KOHLER_ERR_ARG;
   if (dt == KOHLER_U8 && s->M > 256) return KOHLER_ERR_ARG;
   const int es = dt == KOHLER_U8 ? 1 : 2;
@@ -433,6 +450,45 @@ int submit_frame(kohler_server* s, const void* host_frame, kohler_dtype dt, int6
   f->dpitch = ((width * es + 127) / 128) * 128;
   f->bytes = (size_t)f->dpitch * height;
   f->t_submit = Clock::now();
+  if (borrow) {
+    // the caller's buffer stays valid until the ticket is polled: it is copied
+    // asynchronously (several copies in flight), by this call when the frame
+    // can be admitted at once, else by the scheduler when it is admitted
+    f->borrowed = host_frame;
+    f->src_pitch = pitch_bytes;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+      delete f;
+      return KOHLER_ERR_ARG;
+    }
+    f->ticket = s->next_ticket++;
+    s->frames[f->ticket] = f;
+    ++s->n_submitted;
+    *ticket = f->ticket;
+    void* d = (s->queue.empty() && !s->free_slots.empty()) ? s->dev_alloc(f->bytes) : nullptr;
+    if (d) {
+      f->dev = d;
+      f->slot = s->free_slots.back();
+      s->free_slots.pop_back();
+      cudaError_t e = cudaMemcpy2DAsync(d, f->dpitch, host_frame, pitch_bytes, width * es, height,
+                                        cudaMemcpyHostToDevice, s->copy);
+      f->copied = s->get_event();
+      if (e == cudaSuccess && f->copied) e = cudaEventRecord(f->copied, s->copy);
+      if (e != cudaSuccess || !f->copied) {
+        f->status = e != cudaSuccess ? status_of(e) : KOHLER_ERR_CUDA;
+        f->state = FrameState::Done;
+        ++s->n_finished;
+        s->cv_done.notify_all();
+        return KOHLER_OK;  // the error is reported by kohler_poll
+      }
+      f->state = FrameState::Copying;
+      s->copying.push_back(f);
+    } else {
+      s->queue.push_back(f);
+    }
+    s->cv_work.notify_one();
+    return KOHLER_OK;
+  }
   // Direct admission: when no frame waits ahead of this one and a slot and
   // device memory are free, the frame is copied from the caller's buffer
   // straight into its device buffer (no staging copy); the call returns once
@@ -514,6 +570,11 @@ extern "C" {
 int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                   int64_t pitch_bytes, uint64_t* ticket) {
   return submit_frame(s, host_frame, dt, width, height, pitch_bytes, nullptr, 0, ticket);
+}
+
+int kohler_submit_borrowed(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
+                           int64_t pitch_bytes, uint64_t* ticket) {
+  return submit_frame(s, host_frame, dt, width, height, pitch_bytes, nullptr, 0, ticket, true);
 }
 
 int kohler_submit_segment(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,

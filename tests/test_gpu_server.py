@@ -33,11 +33,18 @@ def K():
 
 
 class Server:
-    def __init__(self, K, M=256, budget=0, inflight=0):
+    def __init__(self, K, M=256, budget=0, inflight=0, staging=0):
         self.K = K
         self.L = K.lib()
         self.h = ctypes.c_void_p()
-        assert self.L.kohler_server_create(ctypes.byref(self.h), M, MAX_K, budget, inflight) == 0
+        assert self.L.kohler_server_create_ex(ctypes.byref(self.h), M, MAX_K, budget, inflight, staging) == 0
+
+    def submit_borrowed(self, frame):
+        t = ctypes.c_uint64()
+        code = 1 if frame.dtype == np.uint8 else 2
+        rc = self.L.kohler_submit_borrowed(self.h, frame.ctypes.data, code, frame.shape[1], frame.shape[0],
+                                           frame.strides[0], ctypes.byref(t))
+        return rc, t.value
 
     def submit(self, frame):
         t = ctypes.c_uint64()
@@ -116,6 +123,55 @@ def test_alone_and_mixed(K):
         sub, fin, launches, maxb = s.stats()
         assert sub == fin == 2 * len(fr)
         assert launches <= 2 * len(fr)
+    finally:
+        s.close()
+
+
+def pinned(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+
+
+def test_borrowed_burst_batches(K):
+    # frames submitted without waiting for their copies, from two threads: the
+    # copies overlap, and frames whose copies land while launches are on the GPU
+    # share one launch; every result equals the frame's own, served alone
+    scene = synth.VideoScene(seed=21)
+    sizes = [(1920, 1080), (3840, 2160), (640, 480), (1920, 1080)]
+    fr = [pinned(scene.frame(k, *sizes[k % len(sizes)])) for k in range(32)]
+    want = [expected(f) for f in fr]
+    s = Server(K)
+    try:
+        alone = []
+        for f in fr[:4]:
+            rc, t = s.submit_borrowed(f)
+            assert rc == 0
+            rc, t0, cnt, ts, lat = s.poll(t)
+            assert rc == 0
+            alone.append((t0, cnt, ts))
+        assert alone == want[:4]
+        tickets = [None] * len(fr)
+
+        def produce(idx):
+            for i in idx:
+                rc, t = s.submit_borrowed(fr[i])
+                assert rc == 0
+                tickets[i] = t
+
+        th = [threading.Thread(target=produce, args=(range(j, len(fr), 2),)) for j in range(2)]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        mixed = []
+        for t in tickets:
+            rc, t0, cnt, ts, lat = s.poll(t)
+            assert rc == 0
+            mixed.append((t0, cnt, ts))
+        assert mixed == want
+        sub, fin, launches, maxb = s.stats()
+        assert sub == fin == 4 + len(fr)
+        assert maxb > 1, "no launch took more than one frame"
+        assert launches < 4 + len(fr)
     finally:
         s.close()
 

@@ -6,7 +6,9 @@ with a fixed memory budget): it keeps its scratch in one fixed array of device
 memory instead of a per-stream workspace.  Its results must equal those of
 kohler_analyze_batch bit for bit (the tolerance of every parity test here is
 zero), on two calls in a row, since the array keeps the previous call's
-contents.  This file is named so that pytest collects it last.
+contents.  Every case is also compared with the CPU oracle directly, so that a
+mistake shared by both device paths cannot pass.  This file is named so that
+pytest collects it last.
 """
 import ctypes
 
@@ -14,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import synth
 
 pytestmark = pytest.mark.gpu
@@ -27,9 +30,18 @@ def lib():
     from paper_1707_05062_gb300 import build
 
     build.build()
+    oracle.build()
     import paper_1707_05062_gb300 as K
 
     return K
+
+
+def check_oracle(got, a, M, nb, what):
+    card, sumc, c, ts, cnt, t0 = oracle.analyze(a, M, MAX_K, nbhd=nb)
+    assert np.array_equal(got[0].view(np.uint64), card), what
+    assert np.array_equal(got[1].view(np.uint64), sumc), what
+    assert np.array_equal(got[2], c), what
+    assert np.array_equal(got[3], ts) and int(got[4][0]) == cnt and int(got[5][0]) == t0, what
 
 
 def regular(K, img, M, nb=4):
@@ -77,6 +89,7 @@ def test_no_alloc_matches_regular_twice(lib, name, make, M):
         assert status == 0
         for g, w in zip(got, want):
             assert np.array_equal(g, w), f"{name}: call {call} differs"
+        check_oracle(got, a, M, 4, f"{name}: call {call} against the oracle")
 
 
 @pytest.mark.parametrize("nb", [8, 6])
@@ -92,6 +105,7 @@ def test_no_alloc_other_neighbourhoods(lib, name, make, M, nb):
         assert status == 0
         for g, w in zip(got, want):
             assert np.array_equal(g, w), f"{name} N{nb}: call {call} differs"
+        check_oracle(got, a, M, nb, f"{name} N{nb}: call {call} against the oracle")
 
 
 def test_no_alloc_range_and_limits(lib):
