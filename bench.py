@@ -420,7 +420,8 @@ def bench_e2e(args, pool_np, M, rank, dist):
     total = sum_over_ranks(dist, float(px * steps))
     return {"value": total / dt / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(px),
             "d2h_bytes_per_step": int(M * 8 * 3 + MAX_K * 4 + 8), "steps": steps,
-            "call": "kohler_analyze_host (pinned host image -> host curve and thresholds)"}
+            "call": "kohler_analyze_host (pinned host image -> host curve and thresholds; "
+                    "recorded as one CUDA graph per geometry and replayed)"}
 
 
 # ----------------------------------------------------------------------------- batched and served forms
@@ -1093,7 +1094,7 @@ def bench_reference(args, rank, world):
 
 # Small fixed workloads for ncu captures of one kernel: a few untimed launches,
 # then `launches` launches of the case, nothing else on the GPU.
-NCU_CASES = ("u16_batch16", "u16_batch16_tuned", "n8_18mp", "n6_18mp", "segment_18mp")
+NCU_CASES = ("u8_18mp", "u16_batch16", "u16_batch16_tuned", "n8_18mp", "n6_18mp", "segment_18mp")
 
 
 def ncu_case(name: str, launches: int = 3) -> int:
@@ -1127,6 +1128,8 @@ def ncu_case(name: str, launches: int = 3) -> int:
             res = K.analyze_batch([img], 256, 6)
             out = torch.empty_like(img)
             run = lambda: K.segment(img, 256, res[3][0], res[4][0], out=out)
+        elif name == "u8_18mp":
+            run = lambda: K.analyze_batch([img], 256, MAX_K)
         else:
             nb = 8 if name == "n8_18mp" else 6
             run = lambda: K.analyze_batch([img], 256, MAX_K, nbhd=nb)

@@ -183,8 +183,8 @@ int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int6
  * epilogue with the next call's pass.  Allow it only when the stream's kernel
  * right before each call does not write that call's images (for instance,
  * when it is the library's own previous call, or when the images were written
- * before it).  The library's internal streams (server, host path) allow it.
- * Calls on other streams are unaffected.  The paper has no counterpart: this
+ * before it).  The server's internal stream allows it.  Calls on other streams
+ * are unaffected.  The paper has no counterpart: this
  * is a scheduling choice of this implementation. */
 int kohler_stream_overlap(void* cuda_stream, int32_t enable);
 

@@ -29,6 +29,7 @@ constexpr int kMaxSmemBins = 4096;   // largest M reduced in shared memory
 struct Workspace {
   int device = -1;
   cudaStream_t stream = nullptr;
+  uint64_t gen = 0;  // bumped at every (re)allocation: graphs recorded on older memory are stale
   void* mem = nullptr;
   int slots = 0, hist_words = 0, cand_stride = 0;
   unsigned long long* hist = nullptr;
@@ -145,6 +146,7 @@ int get_workspace(cudaStream_t stream, int slots, int hist_words, int cand_strid
   }
   char* p = static_cast<char*>(mem);
   w->mem = mem;
+  ++w->gen;
   w->hist = reinterpret_cast<unsigned long long*>(p);
   w->done = reinterpret_cast<unsigned*>(p + hist_b);
   w->err = reinterpret_cast<unsigned*>(p + hist_b + done_b);
@@ -1011,6 +1013,20 @@ const char* kohler_strerror(int status) {
 
 // ----------------------------------------------------------------------------- host-buffer path
 namespace {
+// A recorded host-path call: its band copies, launches and result copies as
+// one CUDA graph, replayed for later calls with the same image geometry and
+// arguments from pinned memory; only the copies' source addresses change.
+struct HostGraph {
+  std::tuple<int64_t, int64_t, int64_t, int, int, int, int> key;  // W, H, pitch, dtype, M, nbhd, max_k
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  uint64_t ws_gen = 0;                  // the compute stream's workspace it was recorded on
+  std::vector<cudaGraphNode_t> copies;  // host-to-device copy nodes (one contiguous band each)
+  std::vector<int64_t> src_off;         // their source offsets in the host image
+  std::vector<void*> dst;               // their device destinations
+  std::vector<size_t> bytes;            // their sizes
+};
+
 struct HostPath {
   int device = -1;
   cudaStream_t compute = nullptr, copy = nullptr;
@@ -1020,7 +1036,18 @@ struct HostPath {
   size_t dout_bytes = 0;
   void* hout = nullptr;  // pinned mirror of dout
   std::vector<cudaEvent_t> ev;
+  std::vector<HostGraph> graphs;      // at most kHostGraphs, oldest replaced first
+  std::vector<decltype(HostGraph::key)> seen;  // keys called once from pinned memory (recorded on the second call)
+  bool no_graphs = false;  // a recording failed once: this path stays eager
 };
+constexpr size_t kHostGraphs = 4;
+
+void drop_graph(HostGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  g.exec = nullptr;
+  g.graph = nullptr;
+}
 std::mutex g_host_mu;
 std::map<int, HostPath*> g_host;
 
@@ -1035,11 +1062,9 @@ void release_host_path(int dev) {
   if (h->dimg) cudaFree(h->dimg);
   if (h->dout) cudaFree(h->dout);
   if (h->hout) cudaFreeHost(h->hout);
+  for (auto& g : h->graphs) drop_graph(g);
   for (cudaEvent_t x : h->ev) cudaEventDestroy(x);
-  if (h->compute) {
-    kohler_stream_overlap(h->compute, 0);
-    cudaStreamDestroy(h->compute);
-  }
+  if (h->compute) cudaStreamDestroy(h->compute);
   if (h->copy) cudaStreamDestroy(h->copy);
   delete h;
   g_host.erase(it);
@@ -1055,7 +1080,12 @@ int host_path(HostPath** out, size_t img_bytes, size_t out_bytes, int bands) {
     h->device = dev;
     if ((e = cudaStreamCreateWithFlags(&h->compute, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
     if ((e = cudaStreamCreateWithFlags(&h->copy, cudaStreamNonBlocking)) != cudaSuccess) return status_of(e);
-    kohler_stream_overlap(h->compute, 1);  // only this path's own launches, copies and waits
+  }
+  if (h->dimg_bytes < img_bytes || h->dout_bytes < out_bytes) {
+    // recorded graphs refer to the buffers about to be replaced
+    for (auto& g : h->graphs) drop_graph(g);
+    h->graphs.clear();
+    h->seen.clear();
   }
   if (h->dimg_bytes < img_bytes) {
     if (h->dimg) cudaFree(h->dimg);
@@ -1106,14 +1136,15 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
   const bool packed = pitch_bytes == width * es && (width * es) % 8 == 0;
   const int64_t dpitch = packed ? width * es : ((width * es + 127) / 128) * 128;
   const size_t img_bytes = (size_t)dpitch * height;
-  // bands of rows: copy band b + 1 while band b is reduced (a band needs the first
-  // row of the next band for its lower pairs).  Each band costs four host calls
-  // (copy, event, wait, launch) of several microseconds each, so bands are at
-  // least 8 MB: one per 8 MB, at most 4.
-  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(4, img_bytes / (8 << 20)));
+  // bands of rows: band b is copied together with the first row of band b + 1
+  // (its lower pairs need it), so each band is reduced as soon as its own copy
+  // lands, while the next bands are still copying; after the last copy only the
+  // last band's reduction and the epilogue remain.  Bands of at least 4 MB, at
+  // most 4 (from pinned memory the whole call is one recorded graph, below).
+  const int nbands = (int)std::max<int64_t>(1, std::min<int64_t>(4, img_bytes / (4 << 20)));
   std::lock_guard<std::mutex> lock(g_host_mu);
   HostPath* h = nullptr;
-  rc = host_path(&h, img_bytes, out_bytes, nbands + 1);
+  rc = host_path(&h, img_bytes, out_bytes, nbands + 2);
   if (rc) return rc;
   char* dout = static_cast<char*>(h->dout);
   auto reduce = [&](const kohler_image& im, const std::vector<Band>* band) {
@@ -1123,17 +1154,22 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
                      reinterpret_cast<int32_t*>(dout + o_cnt), reinterpret_cast<int32_t*>(dout + o_t0), h->compute,
                      band, nullptr, nullptr, nb);
   };
-  cudaError_t e = cudaSuccess;
-  {
-    char* dimg = static_cast<char*>(h->dimg);
-    // band edges on multiples of 8 rows
-    std::vector<int32_t> yb(nbands + 1);
-    for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)std::min<int64_t>(height, ((height * b) / nbands + 7) / 8 * 8);
-    yb[nbands] = (int32_t)height;
+  // the whole call's device work on the path's streams: band copies (copy
+  // stream), band reductions (compute stream, each after its own copy and the
+  // next one), then the results and the stream's error word into the pinned mirror
+  Workspace* ws = nullptr;
+  rc = get_workspace(h->compute, 1, 128, cand_ints(2), &ws);
+  if (rc) return rc;
+  char* dimg = static_cast<char*>(h->dimg);
+  std::vector<int32_t> yb(nbands + 1);  // band edges on multiples of 8 rows
+  for (int b = 0; b <= nbands; ++b) yb[b] = (int32_t)std::min<int64_t>(height, ((height * b) / nbands + 7) / 8 * 8);
+  yb[nbands] = (int32_t)height;
+  auto enqueue = [&](const void* src_img) -> int {
+    cudaError_t e = cudaSuccess;
     for (int b = 0; b < nbands && e == cudaSuccess; ++b) {
-      const int64_t r0 = yb[b], r1 = yb[b + 1];
-      if (r1 > r0) {
-        const char* src = static_cast<const char*>(img) + r0 * pitch_bytes;
+      const int64_t r0 = yb[b], r1 = std::min<int64_t>(height, (int64_t)yb[b + 1] + 1);  // + the next band's first row
+      if (yb[b + 1] > yb[b]) {
+        const char* src = static_cast<const char*>(src_img) + r0 * pitch_bytes;
         e = packed ? cudaMemcpyAsync(dimg + r0 * dpitch, src, (size_t)(r1 - r0) * dpitch, cudaMemcpyHostToDevice, h->copy)
                    : cudaMemcpy2DAsync(dimg + r0 * dpitch, dpitch, src, pitch_bytes, width * es, r1 - r0,
                                        cudaMemcpyHostToDevice, h->copy);
@@ -1143,26 +1179,122 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
     if (e != cudaSuccess) return status_of(e);
     const kohler_image im{dimg, width, height, dpitch};
     for (int b = 0; b < nbands; ++b) {
-      // band b reads rows [yb[b] - 1, yb[b + 1]]: wait for its own copy and the next one
-      e = cudaStreamWaitEvent(h->compute, h->ev[std::min(b + 1, nbands - 1)], 0);
+      // band b reads rows [yb[b] - 1, yb[b + 1]]: the row above came with the
+      // previous band (already waited for), the others with its own copy
+      e = cudaStreamWaitEvent(h->compute, h->ev[b], 0);
       if (e != cudaSuccess) return status_of(e);
       if (yb[b + 1] <= yb[b]) continue;
       std::vector<Band> band(1, Band{yb[b], yb[b + 1]});
-      rc = reduce(im, &band);
+      const int r = reduce(im, &band);
+      if (r) return r;
+    }
+    e = cudaMemcpyAsync(h->hout, dout, o_sticky, cudaMemcpyDeviceToHost, h->compute);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(static_cast<char*>(h->hout) + o_sticky, ws->sticky, sizeof(unsigned),
+                          cudaMemcpyDeviceToHost, h->compute);
+    return status_of(e);
+  };
+  // From pinned memory with packed rows the call is recorded once per geometry
+  // (on its second call, when the workspace and every cached launch setting
+  // exist) and then replayed as one graph: one host call instead of one per
+  // copy, wait and launch.  Each band is then one contiguous copy, whose source
+  // a replay can change (CUDA updates one-dimensional copy nodes only).
+  cudaPointerAttributes pa;
+  const bool pinned = packed && cudaPointerGetAttributes(&pa, img) == cudaSuccess && pa.type == cudaMemoryTypeHost;
+  if (!pinned) cudaGetLastError();  // clear the error of a pointer the runtime does not know
+  const auto key = std::make_tuple(width, height, pitch_bytes, (int)dt, (int)M, (int)nb, (int)max_k);
+  HostGraph* hg = nullptr;
+  for (auto& g : h->graphs)
+    if (g.key == key && g.exec && g.ws_gen == ws->gen) hg = &g;
+  cudaError_t e = cudaSuccess;
+  if (pinned && hg) {
+    const char* base = static_cast<const char*>(img);
+    for (size_t k = 0; k < hg->copies.size() && e == cudaSuccess; ++k)
+      e = cudaGraphExecMemcpyNodeSetParams1D(hg->exec, hg->copies[k], hg->dst[k], base + hg->src_off[k], hg->bytes[k],
+                                             cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaGraphLaunch(hg->exec, h->compute);
+    if (e != cudaSuccess) return status_of(e);
+  } else if (pinned && !h->no_graphs && std::find(h->seen.begin(), h->seen.end(), key) != h->seen.end()) {
+    // a stale recording of this key (older workspace) is replaced
+    for (auto it = h->graphs.begin(); it != h->graphs.end();) {
+      if (it->key == key) {
+        drop_graph(*it);
+        it = h->graphs.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    HostGraph g;
+    g.key = key;
+    g.ws_gen = ws->gen;
+    e = cudaStreamBeginCapture(h->compute, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev[nbands], h->compute);  // the copy stream joins the capture
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy, h->ev[nbands], 0);
+    rc = e == cudaSuccess ? enqueue(img) : status_of(e);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(h->compute, &graph);
+    if (rc || ee != cudaSuccess || !graph) {
+      // not recordable here: this call and the later ones run eagerly
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      h->no_graphs = true;
+      rc = enqueue(img);
       if (rc) return rc;
+      e = cudaStreamSynchronize(h->compute);
+      if (e != cudaSuccess) return status_of(e);
+      goto results;
+    }
+    g.graph = graph;
+    size_t n = 0;
+    e = cudaGraphGetNodes(graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(graph, nodes.data(), &n);
+    const char* lo = static_cast<const char*>(img);
+    const char* hi = lo + (size_t)pitch_bytes * (size_t)height;
+    for (size_t k = 0; k < n && e == cudaSuccess; ++k) {
+      cudaGraphNodeType t;
+      if ((e = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeMemcpy) continue;
+      cudaMemcpy3DParms cp = {};
+      if ((e = cudaGraphMemcpyNodeGetParams(nodes[k], &cp)) != cudaSuccess) break;
+      const char* src = static_cast<const char*>(cp.srcPtr.ptr);
+      if (src >= lo && src < hi) {
+        // packed rows: the band starting at byte off of the host image is the
+        // contiguous copy of its rows to the same offset of the device image
+        const int64_t off = src - lo;
+        int b = 0;
+        while (b < nbands && (int64_t)yb[b] * pitch_bytes != off) ++b;
+        if (b == nbands) {
+          e = cudaErrorInvalidValue;
+          break;
+        }
+        g.copies.push_back(nodes[k]);
+        g.src_off.push_back(off);
+        g.dst.push_back(dimg + (int64_t)yb[b] * dpitch);
+        g.bytes.push_back((size_t)(std::min<int64_t>(height, (int64_t)yb[b + 1] + 1) - yb[b]) * (size_t)dpitch);
+      }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(g.exec, h->compute);
+    if (e != cudaSuccess) {
+      drop_graph(g);
+      return status_of(e);
+    }
+    if (h->graphs.size() >= kHostGraphs) {
+      drop_graph(h->graphs.front());
+      h->graphs.erase(h->graphs.begin());
+    }
+    h->graphs.push_back(g);
+  } else {
+    rc = enqueue(img);
+    if (rc) return rc;
+    if (pinned && std::find(h->seen.begin(), h->seen.end(), key) == h->seen.end()) {
+      if (h->seen.size() >= 4 * kHostGraphs) h->seen.erase(h->seen.begin());
+      h->seen.push_back(key);
     }
   }
-  // results and the stream's error word back to the host in one wait: copies into
-  // the pinned mirror, then host copies
-  Workspace* ws = nullptr;
-  rc = get_workspace(h->compute, 1, 128, cand_ints(2), &ws);
-  if (rc) return rc;
-  e = cudaMemcpyAsync(h->hout, dout, o_sticky, cudaMemcpyDeviceToHost, h->compute);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(static_cast<char*>(h->hout) + o_sticky, ws->sticky, sizeof(unsigned), cudaMemcpyDeviceToHost,
-                        h->compute);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->compute);
+  e = cudaStreamSynchronize(h->compute);
   if (e != cudaSuccess) return status_of(e);
+results:
   const char* ho = static_cast<const char*>(h->hout);
   unsigned bits = 0;
   memcpy(&bits, ho + o_sticky, sizeof(bits));

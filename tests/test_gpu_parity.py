@@ -383,6 +383,34 @@ def test_analyze_host_in_bands():
     assert_same(k.analyze_host(view, 256, MAX_K), expect(np.ascontiguousarray(view), 256), "18 Mpx, pitch 5200")
 
 
+def test_analyze_host_recorded_replays():
+    # from pinned memory the host path is recorded as one CUDA graph on a
+    # geometry's second call and replayed afterwards with the new image's
+    # address: every call must give that image's own exact result, across
+    # geometries (banded and not), a pageable call in between, a range error
+    # and a workspace that grows in the middle (which invalidates the recordings)
+    k = K()
+    shapes = [(3456, 5184, 256), (600, 1024, 256), (300, 1000, 200)]
+    for rnd in range(3):
+        for si, (h, w, M) in enumerate(shapes):
+            imgs = [synth.random_image(1000 * rnd + 10 * si + j, w, h, M) for j in range(3)]
+            wants = [expect(a, M) for a in imgs]
+            pins = [torch.from_numpy(a).pin_memory() for a in imgs]
+            for j in (0, 1, 2, 1, 0):
+                assert_same(k.analyze_host(pins[j], M, MAX_K), wants[j], f"round {rnd} {w}x{h} image {j}")
+            assert_same(k.analyze_host(imgs[2], M, MAX_K), wants[2], "pageable between replays")
+            if M < 256:  # a pixel >= M (M = 256 cannot be exceeded in uint8)
+                bad = imgs[0].copy()
+                bad[h // 2, w // 3] = M
+                with pytest.raises(k.KohlerError) as e:
+                    k.analyze_host(torch.from_numpy(bad).pin_memory(), M, MAX_K)
+                assert e.value.status == k.ERR_RANGE
+                assert_same(k.analyze_host(pins[1], M, MAX_K), wants[1], "after a range error")
+        if rnd == 1:  # a larger M grows the host path's workspace
+            u = synth.smooth_image(77, 516, 130, 4096, np.uint16)
+            assert_same(k.analyze_host(torch.from_numpy(u.view(np.int16)).pin_memory(), 4096, MAX_K), expect(u, 4096))
+
+
 # ------------------------------------------------------------------------ workloads at full size
 def test_blobs_256():
     img = synth.blobs_image()
