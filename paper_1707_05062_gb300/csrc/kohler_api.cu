@@ -399,14 +399,17 @@ bool route_ok(Pass p, Pass r) {
   }
 }
 
-// The launch parameters used when nothing is tuned.
+// The launch parameters used when nothing is tuned.  The uint16 pass takes 8
+// pixels per lane (one 16-byte load: the DRAM sectors of a row are read once;
+// images without 16-byte rows fall back to 4), 16 warps per histogram copy and
+// 64 rows per warp, the autotuner's choice on the 16-image 12-bit batch.
 TuneVal default_tune(Pass p) {
   TuneVal t;
   t.route = (int)p;
-  t.warps = kFastWarps;
-  t.px = 4;
+  t.warps = p == Pass::FastU16 ? 16 : kFastWarps;
+  t.px = p == Pass::FastU16 ? 8 : 4;
   t.per_sm = 0;
-  t.upw = is_fast_u8(p) ? 2 : kRowsPerWarp;
+  t.upw = is_fast_u8(p) ? 2 : (p == Pass::FastU16 ? 64 : kRowsPerWarp);
   return t;
 }
 

@@ -1,6 +1,8 @@
 // Device code of libkohler: the uint8 strip pass for the 8- and hexagonal
 // 6-neighbourhoods (k_u8n), on the region layout, ring and fold of k_u8h.
 #pragma once
+#include <type_traits>
+
 #include "kohler_u8h.cuh"
 
 namespace kohler {
@@ -60,9 +62,8 @@ __device__ __forceinline__ void u8n_load(uint32_t ra, uint32_t K, bool lastc, ui
 // when padded; upper pairs that exist) and its constant low part (- padded
 // lower pairs - upper pairs).
 template <int NB>
-__device__ __forceinline__ void u8n_consts(int y, int H, bool leftb, bool lastc, uint32_t& D0, uint32_t& Dm,
-                                           uint32_t& D7, bool& own_dr, bool& own_dl) {
-  const bool odd = (y & 1) != 0;
+__device__ __forceinline__ void u8n_consts_odd(bool odd, int y, int H, bool leftb, bool lastc, uint32_t& D0,
+                                               uint32_t& Dm, uint32_t& D7, bool& own_dr, bool& own_dl) {
   own_dr = NB == 8 || (NB == 6 && odd);
   own_dl = NB == 8 || (NB == 6 && !odd);
   const bool up = y > 0;
@@ -79,6 +80,11 @@ __device__ __forceinline__ void u8n_consts(int y, int H, bool leftb, bool lastc,
   Dm = word(false, false);
   D0 = word(leftb, false);
   D7 = word(false, lastc);
+}
+template <int NB>
+__device__ __forceinline__ void u8n_consts(int y, int H, bool leftb, bool lastc, uint32_t& D0, uint32_t& Dm,
+                                           uint32_t& D7, bool& own_dr, bool& own_dl) {
+  u8n_consts_odd<NB>((y & 1) != 0, y, H, leftb, lastc, D0, Dm, D7, own_dr, own_dl);
 }
 
 // The updates of one row of 8 pixels (A: row y, AL the pixel left of A[0]; B,
@@ -297,19 +303,28 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         // whole groups: rows y .. y + 3 with lower rows y + 1 .. y + 4 (the
         // group's four rows); the row buffers alternate roles
         int y = ya;
-        auto one = [&](const uint32_t(&A)[9], uint32_t AL, uint32_t(&B)[9], uint32_t& BL, uint32_t r, int yy) {
+        // the row's parity is a compile-time constant in each instance (N6 owns
+        // a different lower diagonal on even and odd rows), chosen once per group
+        auto one = [&](auto oddc, const uint32_t(&A)[9], uint32_t AL, uint32_t(&B)[9], uint32_t& BL, uint32_t r,
+                       int yy) {
           u8n_load(rg.cur + r * kRowBytesN, K, lastc, B, BL);
           uint32_t D0, Dm, D7;
           bool own_dr, own_dl;
-          u8n_consts<NB>(yy, H, leftb, lastc, D0, Dm, D7, own_dr, own_dl);
+          u8n_consts_odd<NB>(decltype(oddc)::value, yy, H, leftb, lastc, D0, Dm, D7, own_dr, own_dl);
           if (act) u8n_row<NB, CHECK, false>(A, AL, B, BL, mU, D0, Dm, D7, own_dr, own_dl, leftb, lastc, C, vmax);
+        };
+        auto group = [&](auto oddc) {
+          using E = std::integral_constant<bool, decltype(oddc)::value>;
+          using O = std::integral_constant<bool, !decltype(oddc)::value>;
+          one(E{}, Pc, PcL, Pn, PnL, 0u, y);
+          one(O{}, Pn, PnL, Pc, PcL, 1u, y + 1);
+          one(E{}, Pc, PcL, Pn, PnL, 2u, y + 2);
+          one(O{}, Pn, PnL, Pc, PcL, 3u, y + 3);
         };
         while (y + kGroupRows <= ylim) {
           wait_group();
-          one(Pc, PcL, Pn, PnL, 0u, y);
-          one(Pn, PnL, Pc, PcL, 1u, y + 1);
-          one(Pc, PcL, Pn, PnL, 2u, y + 2);
-          one(Pn, PnL, Pc, PcL, 3u, y + 3);
+          if (NB == 6 && (y & 1)) group(std::true_type{});
+          else group(std::false_type{});
           y += kGroupRows;
           jr += kGroupRows;
           __syncwarp();
