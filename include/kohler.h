@@ -155,6 +155,41 @@ int kohler_analyze_host(const void* img, kohler_dtype dt, int64_t width, int64_t
                         int32_t M, kohler_nbhd nb, int32_t max_k, uint64_t* card, uint64_t* sumc,
                         double* curve, int32_t* out_t, int32_t* out_count, int32_t* out_t0);
 
+/* ---------------------------------------------------------------- row bands
+ * One image split by rows, e.g. over the GPUs of a node (Section 3.3: the
+ * method sums per-thread accumulators; here per-band histograms).  The pairs a
+ * band [y0, y1) owns are the right pairs of its rows and the lower pairs of its
+ * rows (row y with row y + 1, when y + 1 < height); every pair of the image
+ * belongs to exactly one band.  The histograms of Section 2 of kohler_curve's
+ * exact rewrite (H_lo: the pairs' lower values, H_hi: their higher values,
+ * H_s: their sums) add over bands, so the whole image's curve comes from the
+ * element-wise sum of the bands' histograms.
+ *
+ * kohler_band_histograms adds band [y0, y1)'s histograms to `hist`, a device
+ * uint64[1024] (H_lo at [0, 256), H_hi at [256, 512), H_s at [512, 1024)),
+ * asynchronously on cuda_stream.  `rows` points at image row first_row of a
+ * buffer of n_rows rows (pitch_bytes apart) that holds at least the rows
+ * max(0, y0 - 3) .. min(height, y1 + 1) - 1: the band, the row below it, and
+ * three rows above it (the upper pairs' order and the strip pass's row
+ * groups).  Only 16-byte aligned uint8 images (rows, pitch and width multiples
+ * of 16 bytes), the 4-neighbourhood and M <= 256: KOHLER_ERR_UNSUPPORTED
+ * otherwise; KOHLER_ERR_ARG for inconsistent rows or band.  An empty band
+ * (y0 == y1) adds nothing and launches nothing.  A pixel >= M in
+ * the band makes the next kohler_stream_status on the stream return
+ * KOHLER_ERR_RANGE.
+ *
+ * kohler_histograms_curve turns summed histograms (uint8 image of width x
+ * height, M <= 256) into card, sumc, curve (may be NULL), the ranked
+ * thresholds and t0, as kohler_analyze_batch does for one image, on
+ * cuda_stream; out_status (may be NULL): KOHLER_OK.  `hist` is cleared (all
+ * zero) for reuse. */
+int kohler_band_histograms(const void* rows, int64_t first_row, int64_t n_rows, kohler_dtype dt, int64_t width,
+                           int64_t height, int64_t pitch_bytes, int64_t y0, int64_t y1, int32_t M, kohler_nbhd nb,
+                           uint64_t* hist, void* cuda_stream);
+int kohler_histograms_curve(uint64_t* hist, kohler_dtype dt, int64_t width, int64_t height, int32_t M, int32_t max_k,
+                            uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count,
+                            int32_t* out_t0, int32_t* out_status, void* cuda_stream);
+
 /* kohler_analyze_batch for one device image, without any device allocation (the
  * paper has no counterpart; this serves callers that cannot allocate while they
  * run, e.g. inside a real-time loop or under a fixed memory budget).  Scratch

@@ -66,6 +66,8 @@ def lib():
             L.kohler_analyze_host.argtypes = [p, i, i64, i64, i64, i32, i, i32, p, p, p, p, p, p]
             L.kohler_stream_status.argtypes = [p]
             L.kohler_stream_overlap.argtypes = [p, i32]
+            L.kohler_band_histograms.argtypes = [p, i64, i64, i, i64, i64, i64, i64, i64, i32, i, p, p]
+            L.kohler_histograms_curve.argtypes = [p, i, i64, i64, i32, i32, p, p, p, p, p, p, p, p]
             L.kohler_test_inject.argtypes = [i32, i32]
             L.kohler_segment.argtypes = [p, i, i64, i64, i64, i32, p, p, i32, p, i64, p]
             if hasattr(L, "kohler_analyze_noalloc"):
@@ -84,7 +86,8 @@ def lib():
             L.kohler_strerror.restype = ctypes.c_char_p
             for name in ("kohler_curve", "kohler_curve_batch", "kohler_thresholds", "kohler_analyze_batch",
                          "kohler_analyze_host", "kohler_stream_status", "kohler_release", "kohler_segment",
-                         "kohler_stream_overlap", "kohler_test_inject"):
+                         "kohler_stream_overlap", "kohler_test_inject", "kohler_band_histograms",
+                         "kohler_histograms_curve"):
                 getattr(L, name).restype = i
             if hasattr(L, "kohler_server_create"):
                 L.kohler_server_create.argtypes = [p, i32, i32, ctypes.c_size_t, i32]
@@ -119,6 +122,70 @@ def test_inject(kind: int, count: int):
     """Test hook (kohler_test_inject): host-side injected allocation failures
     (FAULT_ALLOC) or ring-wait failures of the strip pass (FAULT_RING_WAIT)."""
     _check(lib().kohler_test_inject(kind, count), "kohler_test_inject")
+
+
+HIST_WORDS = 1024  # uint64 words of the histograms of a uint8 image: H_lo, H_hi (256 each), H_s (512)
+
+
+def row_bands(height: int, n: int):
+    """[y0, y1) of n bands of rows covering [0, height), in order (empty bands
+    when n > height)."""
+    return [(height * k // n, height * (k + 1) // n) for k in range(n)]
+
+
+def band_rows(height: int, y0: int, y1: int):
+    """The rows a band [y0, y1) must hold: three above it, the band, one below."""
+    return max(0, y0 - 3), min(height, y1 + 1)
+
+
+def band_histograms(rows: torch.Tensor, first_row: int, height: int, y0: int, y1: int, M: int,
+                    hist: torch.Tensor = None, stream=None) -> torch.Tensor:
+    """Adds the histograms of the pairs band [y0, y1) owns to `hist` (int64[1024]
+    on the device; allocated and zeroed if None) and returns it.  `rows` holds
+    image rows first_row .. first_row + rows.shape[0] - 1 (kohler_band_histograms)."""
+    if hist is None:
+        hist = torch.zeros(HIST_WORDS, dtype=torch.int64, device=rows.device)
+    ptr, w, n, pitch = _image(rows)
+    _check(lib().kohler_band_histograms(ptr, first_row, n, _dtype_code(rows), w, height, pitch, y0, y1, M, KOHLER_N4,
+                                        hist.data_ptr(), _stream(stream)), "kohler_band_histograms")
+    return hist
+
+
+def histograms_curve(hist: torch.Tensor, width: int, height: int, M: int, max_k: int, *, stream=None):
+    """(card, sumc, curve, out_t, count, t0) from summed band histograms
+    (kohler_histograms_curve); clears `hist`."""
+    dev = hist.device
+    card = torch.empty(M, dtype=torch.int64, device=dev)
+    sumc = torch.empty(M, dtype=torch.int64, device=dev)
+    c = torch.empty(M, dtype=torch.float64, device=dev)
+    out_t = torch.empty(max(max_k, 1), dtype=torch.int32, device=dev)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    t0 = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(lib().kohler_histograms_curve(hist.data_ptr(), KOHLER_U8, width, height, M, max_k, card.data_ptr(),
+                                         sumc.data_ptr(), c.data_ptr(), out_t.data_ptr(), cnt.data_ptr(),
+                                         t0.data_ptr(), None, _stream(stream)), "kohler_histograms_curve")
+    return card, sumc, c, out_t[:max_k], cnt, t0
+
+
+def analyze_row_band(rows: torch.Tensor, first_row: int, width: int, height: int, band, M: int, max_k: int,
+                     group=None, stream=None):
+    """One rank's part of the row-band split of one image over the ranks of
+    `group` (torch.distributed, one band per rank, for instance `row_bands(height,
+    world)[rank]`): this band's histograms, one sum over the ranks (the only
+    exchange: 1024 int64), then the curve and thresholds, on every rank."""
+    hist = band_histograms(rows, first_row, height, band[0], band[1], M, stream=stream)
+    reduce_histograms(hist, group)
+    return histograms_curve(hist, width, height, M, max_k, stream=stream)
+
+
+def reduce_histograms(hist: torch.Tensor, group=None) -> torch.Tensor:
+    """Sums band histograms (or any per-band counts) over the ranks of `group`
+    in place; a no-op without an initialised process group."""
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(hist, op=dist.ReduceOp.SUM, group=group)
+    return hist
 
 
 def _check(rc: int, what: str):

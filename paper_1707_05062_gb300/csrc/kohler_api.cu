@@ -1317,6 +1317,125 @@ results:
   return rc;
 }
 
+// ----------------------------------------------------------------------------- row bands of one image
+// One image split by rows over several devices (or calls): each band adds the
+// histograms of the pairs it owns (the right pairs of its rows and the lower
+// pairs of its rows) to a caller buffer; the buffers are summed (for instance by
+// an all-reduce); the epilogue runs once on the sum.  Every pair belongs to one
+// band, so the sum is the whole image's histograms, exactly.
+int kohler_band_histograms(const void* rows, int64_t first_row, int64_t n_rows, kohler_dtype dt, int64_t width,
+                           int64_t height, int64_t pitch_bytes, int64_t y0, int64_t y1, int32_t M, kohler_nbhd nb,
+                           uint64_t* hist, void* cuda_stream) {
+  int rc = check_common(dt, M, nb);
+  if (rc) return rc;
+  if (!rows || !hist || width < 1 || height < 1 || y0 < 0 || y1 > height || y0 > y1 || first_row < 0 || n_rows < 1 ||
+      first_row + n_rows > height || width > ((int64_t)1 << 30) || height > ((int64_t)1 << 30) || pitch_bytes < width)
+    return KOHLER_ERR_ARG;
+  if (y0 == y1) return KOHLER_OK;  // an empty band owns no pairs
+  // the band's rows, the one above it (its upper pairs' flags) and the one below
+  // it (its lower pairs), and the ring's alignment of each run's first group
+  // (three rows above the band) must be held
+  if (first_row > std::max<int64_t>(0, y0 - 3) || first_row + n_rows < std::min<int64_t>(height, y1 + 1))
+    return KOHLER_ERR_ARG;
+  if (dt != KOHLER_U8 || nb != KOHLER_N4 || ((uintptr_t)rows & 15) || (pitch_bytes & 15) || width % 16)
+    return KOHLER_ERR_UNSUPPORTED;  // the uint8 strip pass only
+  const int64_t strips = (width + u8h::kStripPx - 1) / u8h::kStripPx;
+  if (strips * height >= ((int64_t)1 << 32)) return KOHLER_ERR_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  Workspace* ws = nullptr;
+  rc = get_workspace(stream, 1, hist_words_for(dt, M), cand_ints(M), &ws);
+  if (rc) return rc;
+  LaunchParams P;
+  memset(&P, 0, sizeof(P));
+  P.n = 1;
+  P.M = M;
+  P.bins = 256;
+  P.hist = reinterpret_cast<unsigned long long*>(hist);  // the caller's buffer: slot 0
+  P.hist_stride = hist_words_for(dt, M);
+  P.done = ws->done;
+  P.err = ws->err;
+  P.sticky = ws->sticky;
+  P.cand = ws->cand;
+  P.cand_stride = ws->cand_stride;
+  ImgDesc& d = P.img[0];
+  d.base = static_cast<const unsigned char*>(rows) - first_row * pitch_bytes;  // image row 0 (not read: tensor copies)
+  d.pitch = pitch_bytes;
+  d.W = (int32_t)width;
+  d.H = (int32_t)height;
+  d.y0 = (int32_t)y0;
+  d.y1 = (int32_t)y1;
+  d.strips = (int32_t)strips;
+  d.units_total = (uint32_t)(strips * height);
+  d.tma_y0 = (int32_t)first_row;
+  P.total_rs = strips * (y1 - y0);
+  KernelInfo k = kernel_for(M == 256 ? Pass::HistU8 : Pass::HistU8Check, 256, true);
+  P.smem_bytes = (int32_t)k.smem;
+  const int grid = grid_for(k, P.total_rs, default_tune(Pass::HistU8).upw);
+  ImgMaps<1> T;
+  rc = encode_u8_rows(&T.map[0], rows, width, n_rows, pitch_bytes, u8h::kBoxW, (uint32_t)u8h::kGroupRows);
+  if (rc) return rc;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(k.threads);
+  cfg.dynamicSmemBytes = k.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = kohler::overlap_allowed(stream) ? 1 : 0;
+  void* args[] = {&P, &T};
+  cudaError_t e = cudaLaunchKernelExC(&cfg, k.fn, args);
+  // a range error went to the stream's error word; the slot's bits are cleared
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws->err, 0, sizeof(unsigned), stream);
+  return status_of(e);
+}
+
+int kohler_histograms_curve(uint64_t* hist, kohler_dtype dt, int64_t width, int64_t height, int32_t M, int32_t max_k,
+                            uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t, int32_t* out_count,
+                            int32_t* out_t0, int32_t* out_status, void* cuda_stream) {
+  int rc = check_common(dt, M, KOHLER_N4);
+  if (rc) return rc;
+  if (dt != KOHLER_U8) return KOHLER_ERR_UNSUPPORTED;
+  if (!hist || !card || !sumc || !out_count || !out_t0 || max_k < 0 || (max_k > 0 && !out_t) || width < 1 ||
+      height < 1)
+    return KOHLER_ERR_ARG;
+  cudaStream_t stream = (cudaStream_t)cuda_stream;
+  Workspace* ws = nullptr;
+  rc = get_workspace(stream, 1, hist_words_for(dt, M), cand_ints(M), &ws);
+  if (rc) return rc;
+  LaunchParams P;
+  memset(&P, 0, sizeof(P));
+  P.n = 1;
+  P.M = M;
+  P.bins = 256;
+  P.max_k = max_k;
+  P.card = card;
+  P.sumc = sumc;
+  P.curve = curve;
+  P.out_t = max_k > 0 ? out_t : nullptr;
+  P.out_count = out_count;
+  P.out_t0 = out_t0;
+  P.out_status = out_status;
+  P.hist = reinterpret_cast<unsigned long long*>(hist);
+  P.hist_stride = hist_words_for(dt, M);
+  P.done = ws->done;
+  P.err = ws->err;
+  P.sticky = ws->sticky;
+  P.cand = ws->cand;
+  P.cand_stride = ws->cand_stride;
+  const size_t epi = epilogue_smem(M, 256, 0);
+  P.smem_bytes = (int32_t)epi;
+  ImgDesc& d = P.img[0];
+  d.W = (int32_t)std::min<int64_t>(width, 1 << 30);
+  d.H = (int32_t)std::min<int64_t>(height, 1 << 30);
+  d.y0 = 0;
+  d.y1 = d.H;  // the epilogue kernel treats it as the image's last band
+  void* args[] = {&P};
+  const cudaError_t e = cudaLaunchKernel((const void*)k_finish, dim3(1), dim3(kEpiThreads), args, epi, stream);
+  return status_of(e);
+}
+
 }  // extern "C"
 
 // ----------------------------------------------------------------------------- allocation-free entry point

@@ -54,6 +54,7 @@ struct ImgDesc {
   int32_t slot;               // workspace slot (histograms, counters)
   int32_t out;                // index into the output arrays
   uint32_t units_total;       // work units of the whole image (all bands): completion count
+  int32_t tma_y0;             // image row of the tensor map's first row (a band held without the rows above it)
 };
 
 struct LaunchParams {

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
             const uint32_t bar = rg.bar0 + 8u * slot;
             fence_proxy_async();
             mbar_expect_tx(bar, kBoxBytes);
-            tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_y0 + p_gi * kGroupRows, bar);
+            tma_2d(rg.ring0 + slot * kSlotBytes, map, p_x0 >> 1, p_y0 + p_gi * kGroupRows - d.tma_y0, bar);
           }
           ++issued;
         }
@@ -466,7 +466,10 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
                      base + (int64_t)kNW * kRowsPerRound < seg_end || (SPLIT && seg_end < r1));
       __syncthreads();
     }
-    if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
+    if (CHECK && vmax > vlimit) {
+      atomicOr(P.err + d.slot, kErrRange);
+      if (SPLIT) atomicOr(P.sticky, kErrRange);  // also seen without the epilogue kernel (a band's histograms)
+    }
     if (img_failed && lane == 0) {
       atomicOr(P.err + d.slot, kErrInternal);
       atomicOr(P.sticky, kErrInternal);
