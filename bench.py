@@ -273,29 +273,36 @@ def bench_ours(args, rank, local, world, dist):
     # launching stream (events inside a block would stop a launch from
     # overlapping the previous one's epilogue).  ms_per_step is the median
     # block over K; p90 is reported beside it.
+    # Every kernel before a call on these streams is the library's own previous
+    # call.  The timed stream is pipelined (kohler_stream_overlap mode 2): each
+    # call's pass overlaps the previous call's epilogue, and two consecutive
+    # calls run side by side on half the SMs each.  `stream` (isolated and
+    # Python-launched references) and `wstream` (the same graph with whole-GPU
+    # launches, reported beside the headline) use mode 1.
     gstream = torch.cuda.Stream(dev)
-    # every kernel before a call on these streams is the library's own previous
-    # call: let each call's pass overlap the previous call's epilogue
-    K.stream_overlap(gstream)
+    wstream = torch.cuda.Stream(dev)
+    K.stream_overlap(gstream, pipeline=True)
+    K.stream_overlap(wstream)
     K.stream_overlap(stream)
     G = 512
 
-    def capture(j0, n):
+    def capture(j0, n, st):
         g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g, stream=gstream):
+        with torch.cuda.graph(g, stream=st):
             for j in range(j0, j0 + n):
-                K.analyze_batch([pool[j % POOL]], M, MAX_K, out=outs, stream=gstream)
+                K.analyze_batch([pool[j % POOL]], M, MAX_K, out=outs, stream=st)
         return g
 
-    with torch.cuda.stream(gstream):
-        for i in range(3):  # creates the library's workspace for this stream before capture
-            K.analyze_batch([pool[i % POOL]], M, MAX_K, out=outs, stream=gstream)
+    for st in (gstream, wstream):
+        with torch.cuda.stream(st):
+            for i in range(3):  # creates the library's workspace for this stream before capture
+                K.analyze_batch([pool[i % POOL]], M, MAX_K, out=outs, stream=st)
     torch.cuda.synchronize(dev)
-    graphs = [capture(j0, min(G, args.steps - j0)) for j0 in range(0, args.steps, G)]
+    graphs = [capture(j0, min(G, args.steps - j0), gstream) for j0 in range(0, args.steps, G)]
 
-    def replay_all():
-        with torch.cuda.stream(gstream):
-            for g in graphs:
+    def replay_all(gs=None, st=None):
+        with torch.cuda.stream(st or gstream):
+            for g in (gs or graphs):
                 g.replay()
 
     replay_all()  # warm replay
@@ -329,6 +336,20 @@ def bench_ours(args, rank, local, world, dist):
         raise RuntimeError(f"timed run reported status {st}")
     dev_s = float(np.median(blocks))
     dev_p90 = float(np.percentile(blocks, 90))
+    # the same K steps with whole-GPU launches (mode 1), a few blocks, for reference
+    wgraphs = [capture(j0, min(G, args.steps - j0), wstream) for j0 in range(0, args.steps, G)]
+    replay_all(wgraphs, wstream)
+    torch.cuda.synchronize(dev)
+    wblocks = []
+    for _ in range(max(5, min(200, R // 4))):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(wstream)
+        replay_all(wgraphs, wstream)
+        b.record(wstream)
+        torch.cuda.synchronize(dev)
+        wblocks.append(a.elapsed_time(b) / 1e3)
+    whole_gpu_ms_per_step = float(np.median(wblocks)) * 1e3 / args.steps
+    del wgraphs
     # the same steps launched one by one from Python through the binding, for reference
     outt = outs
     h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,9 +373,11 @@ def bench_ours(args, rank, local, world, dist):
     host_elapsed = max_over_ranks(dist, t_host)
     total_px = sum_over_ranks(dist, float(px * args.steps))
     value = total_px / elapsed / 1e9
-    mean_launch_s = dev_s / args.steps  # one fused launch (pass + epilogue kernel) per step, back to back
+    # one fused launch (pass + epilogue kernel) per step; with two launches in
+    # flight a launch lasts about two steps, so the rate is taken over the block
+    mean_launch_s = dev_s / args.steps
     peak, peak_src = measured_peak_hbm()
-    achieved = px / mean_launch_s / 1e9  # algorithmic bytes: one read of each 1-byte pixel
+    achieved = px / mean_launch_s / 1e9  # algorithmic bytes: one read of each 1-byte pixel, per step time
     traffic = kernel_traffic("k_u8h", "voronoi_18mp")
     e2e = bench_e2e(args, pool_np, M, rank, dist) if not args.no_e2e else None
     cpu = cpu_baseline(pool_np[0], M) if (rank == 0 and world == 1 and not args.no_cpu) else None
@@ -368,14 +391,18 @@ def bench_ours(args, rank, local, world, dist):
         "config": {"workload": "voronoi_18mp", "image": f"{W}x{H} uint8", "M": M, "max_k": MAX_K,
                    "images_per_step": 1, "per_gpu_pool": f"{POOL} distinct images ({POOL * px / 1e6:.0f} MB) cycled",
                    "l2": "inputs larger than L2 (rotating pool), no flush", "parallelism": f"replicas x{world}",
-                   "launch": f"one CUDA graph of the K fused launches, replayed R = {R} times",
+                   "launch": f"one CUDA graph of the K fused launches, replayed R = {R} times; pipelined stream: "
+                             "two consecutive launches side by side on half the SMs each (programmatic dependent "
+                             "launch)",
                    "timing": {"blocks_R": R, "steps_per_block": args.steps,
+                              "whole_gpu_launches_ms_per_step": whole_gpu_ms_per_step,
                               "block_ms_median": dev_s * 1e3, "block_ms_p90": dev_p90 * 1e3,
                               "ms_per_step_p90": dev_p90 * 1e3 / args.steps,
                               "statistic": "median block / K (p90 beside it); max over ranks"}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "peak_source": f"hbm_gbs of {peak_src}",
                      "kernel": "k_u8h (strip pass) + k_finish (curve, thresholds), one step",
+                     "rate": "algorithmic bytes of the K steps / the timed block (two launches in flight)",
                      "mean_launch_us": mean_launch_s * 1e6,
                      "isolated_launch_p50_us": float(np.median(launch_ms)) * 1e3,
                      "host_launched_us_per_step": host_launched_us},

@@ -210,18 +210,27 @@ int kohler_analyze_noalloc(const void* img, kohler_dtype dt, int64_t width, int6
                            int32_t* out_t, int32_t* out_count, int32_t* out_t0, int32_t* out_status,
                            void* cuda_stream);
 
-/* Allows (enable = 1) or forbids (0, the default) the first kernel of each later
- * call on `cuda_stream` of the current device to start before the stream's
- * previous kernel has finished (programmatic dependent launch).  The library's
- * kernels read their images at once but write global memory only after the
- * previous kernel has finished, so back-to-back calls overlap one call's
- * epilogue with the next call's pass.  Allow it only when the stream's kernel
- * right before each call does not write that call's images (for instance,
- * when it is the library's own previous call, or when the images were written
- * before it).  The server's internal stream allows it.  Calls on other streams
- * are unaffected.  The paper has no counterpart: this
- * is a scheduling choice of this implementation. */
-int kohler_stream_overlap(void* cuda_stream, int32_t enable);
+/* Scheduling of later calls on `cuda_stream` of the current device.
+ * mode 0 (the default): a call's first kernel starts after the stream's
+ * previous kernel has finished.
+ * mode 1 (overlap): the first kernel of each call may start before the
+ * stream's previous kernel has finished (programmatic dependent launch).  The
+ * library's kernels read their images at once but write global memory only
+ * after the previous kernel has finished, so back-to-back calls overlap one
+ * call's epilogue with the next call's pass.
+ * mode 2 (pipelined): mode 1, and a call with one uint8 image on the strip pass
+ * (16-byte aligned rows, 4-neighbourhood) runs its pass on half of the GPU's
+ * SMs, so that two consecutive calls run side by side and each block's fixed
+ * phases (clearing its bins, its first copies, the fold) are spread over twice
+ * the rows: higher throughput for a stream of such calls, a longer time for a
+ * call on its own (about 1.4x for an 18-Mpixel image).
+ * Allow modes 1 and 2 only when the stream's kernel right before each call
+ * does not write that call's images (for instance, when it is the library's own
+ * previous call, or when the images were written before it).  The server's
+ * internal stream uses mode 1.  Calls on other streams are unaffected.
+ * KOHLER_ERR_ARG for another mode.  The paper has no counterpart: this is a
+ * scheduling choice of this implementation. */
+int kohler_stream_overlap(void* cuda_stream, int32_t mode);
 
 /* Test hooks (the paper has no counterpart).  They make failures happen on the
  * host side, so that error paths can be tested without faulting a GPU:

@@ -111,11 +111,14 @@ def lib():
 FAULT_ALLOC, FAULT_RING_WAIT = 1, 2
 
 
-def stream_overlap(stream=None, enable: bool = True):
+def stream_overlap(stream=None, enable: bool = True, pipeline: bool = False):
     """Lets the first kernel of each later call on `stream` start before the
-    stream's previous kernel ends (kohler_stream_overlap): only for streams
-    whose kernel before each call does not write that call's images."""
-    _check(lib().kohler_stream_overlap(_stream(stream), 1 if enable else 0), "kohler_stream_overlap")
+    stream's previous kernel ends (kohler_stream_overlap mode 1), and with
+    `pipeline` also runs consecutive one-image uint8 calls side by side on half
+    the GPU each (mode 2): only for streams whose kernel before each call does
+    not write that call's images."""
+    mode = (2 if pipeline else 1) if enable else 0
+    _check(lib().kohler_stream_overlap(_stream(stream), mode), "kohler_stream_overlap")
 
 
 def test_inject(kind: int, count: int):

@@ -343,15 +343,18 @@ Occupancy occupancy_of(const KernelInfo& k) {
 
 // Grid size: enough blocks for ~units_per_warp work units per warp, at most one full
 // wave of resident blocks, and at most per_sm blocks per SM (0: as many as fit).
-int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp, int per_sm = 0) {
+int grid_for(const KernelInfo& k, int64_t total_rs, int units_per_warp, int per_sm = 0, int depth = 1) {
   const Occupancy o = occupancy_of(k);
   const int64_t warps = k.threads / 32;
   int64_t want = (total_rs + warps * units_per_warp - 1) / (warps * units_per_warp);
   // one block short of a full wave: the previous launch's last block may still
   // run its epilogue on one slot when this launch starts (programmatic launch),
-  // and a block waiting for that slot would finish last
+  // and a block waiting for that slot would finish last.  With `depth`
+  // launches side by side, each takes 1/depth of the slots less one for its
+  // epilogue block.
   const int64_t slots = (int64_t)o.sms * (per_sm > 0 ? std::min(per_sm, o.per_sm) : o.per_sm);
-  want = std::max<int64_t>(1, std::min<int64_t>(want, slots > 1 ? slots - 1 : 1));
+  const int64_t cap = depth > 1 ? (slots - depth) / depth : slots - 1;
+  want = std::max<int64_t>(1, std::min<int64_t>(want, cap > 1 ? cap : 1));
   return (int)want;
 }
 
@@ -488,7 +491,11 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   if (!split) k.smem = std::max(k.smem, epi);
   P.smem_bytes = (int32_t)(split ? epi : k.smem);
   if (split && kohler::take_wait_fault()) P.fail_wait = 1u;
-  const int grid = grid_for(k, rs, t.upw, t.per_sm);
+  // pipelined streams: a one-image strip pass takes half the GPU, so that the
+  // next call's pass runs beside it and each block's fixed phases (clearing its
+  // bins, its first tensor copies, the fold) are spread over twice the rows
+  const int depth = (split && P.n == 1 && kohler::pipelined(stream)) ? 2 : 1;
+  const int grid = grid_for(k, rs, t.upw, t.per_sm, depth);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(k.threads);
@@ -619,7 +626,7 @@ namespace {
 std::atomic<int> g_alloc_faults{0};  // pending injected allocation failures
 std::atomic<int> g_wait_faults{0};   // pending injected ring-wait failures
 std::mutex g_overlap_mu;
-std::set<std::pair<int, uintptr_t>> g_overlap;  // (device, stream) pairs allowed to overlap
+std::map<std::pair<int, uintptr_t>, int> g_overlap;  // (device, stream) -> overlap mode (1 or 2)
 bool take_one(std::atomic<int>& n) {
   int v = n.load();
   while (v > 0)
@@ -638,12 +645,18 @@ cudaError_t host_malloc(void** p, size_t bytes) {
 }
 bool take_wait_fault() { return take_one(g_wait_faults); }
 
-bool overlap_allowed(cudaStream_t stream) {
+namespace {
+int overlap_mode(cudaStream_t stream) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   std::lock_guard<std::mutex> lock(g_overlap_mu);
-  return g_overlap.count(std::make_pair(dev, (uintptr_t)stream)) != 0;
+  const auto it = g_overlap.find(std::make_pair(dev, (uintptr_t)stream));
+  return it == g_overlap.end() ? 0 : it->second;
 }
+}  // namespace
+
+bool overlap_allowed(cudaStream_t stream) { return overlap_mode(stream) >= 1; }
+bool pipelined(cudaStream_t stream) { return overlap_mode(stream) == 2; }
 
 const char* pass_name(int pass) { return pass >= 0 && pass < kNumPasses ? kPassNames[pass] : "?"; }
 
@@ -932,13 +945,14 @@ int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int
   return KOHLER_OK;
 }
 
-int kohler_stream_overlap(void* cuda_stream, int32_t enable) {
+int kohler_stream_overlap(void* cuda_stream, int32_t mode) {
+  if (mode < 0 || mode > 2) return KOHLER_ERR_ARG;
   int dev = 0;
   const cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return status_of(e);
   std::lock_guard<std::mutex> lock(kohler::g_overlap_mu);
   const auto key = std::make_pair(dev, (uintptr_t)cuda_stream);
-  if (enable) kohler::g_overlap.insert(key);
+  if (mode) kohler::g_overlap[key] = mode;
   else kohler::g_overlap.erase(key);
   return KOHLER_OK;
 }

@@ -42,6 +42,8 @@ bool take_wait_fault();
 // Whether the caller allowed the library's first kernel of a call on `stream`
 // to overlap the stream's previous kernel (kohler_stream_overlap).
 bool overlap_allowed(cudaStream_t stream);
+// Whether calls on the stream are pipelined (kohler_stream_overlap mode 2).
+bool pipelined(cudaStream_t stream);
 
 // ----------------------------------------------------------------- autotuning
 // Launch parameters of one group of images that take the same pass.
