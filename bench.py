@@ -1121,7 +1121,7 @@ def bench_reference(args, rank, world):
 
 # Small fixed workloads for ncu captures of one kernel: a few untimed launches,
 # then `launches` launches of the case, nothing else on the GPU.
-NCU_CASES = ("u8_18mp", "u16_batch16", "u16_batch16_tuned", "n8_18mp", "n6_18mp", "segment_18mp")
+NCU_CASES = ("u8_18mp", "u8_18mp_pipelined", "u16_batch16", "u16_batch16_tuned", "n8_18mp", "n6_18mp", "segment_18mp")
 
 
 def ncu_case(name: str, launches: int = 3) -> int:
@@ -1157,6 +1157,17 @@ def ncu_case(name: str, launches: int = 3) -> int:
             run = lambda: K.segment(img, 256, res[3][0], res[4][0], out=out)
         elif name == "u8_18mp":
             run = lambda: K.analyze_batch([img], 256, MAX_K)
+        elif name == "u8_18mp_pipelined":
+            # the headline's launch configuration: a pipelined stream (half the SMs per pass)
+            ps = torch.cuda.Stream(dev)
+            K.stream_overlap(ps, pipeline=True)
+
+            def run():
+                with torch.cuda.stream(ps):
+                    K.analyze_batch([img], 256, MAX_K, stream=ps)
+                ps.synchronize()
+                if K.stream_status(ps) != K.OK:
+                    raise RuntimeError("pipelined case reported an error")
         else:
             nb = 8 if name == "n8_18mp" else 6
             run = lambda: K.analyze_batch([img], 256, MAX_K, nbhd=nb)
