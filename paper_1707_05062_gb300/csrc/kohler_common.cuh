@@ -477,8 +477,10 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   const ImgDesc& d = P.img[i];
   const int M = P.M, bins = P.bins;
   unsigned long long* h = P.hist + (size_t)d.slot * P.hist_stride;
-  __threadfence();
-  // a pixel >= M, or a ring wait of the strip pass that gave up: outputs zero
+  // The passes' histogram atomics and error bits are visible here: k_finish
+  // runs after griddepcontrol.wait, the completing block of the other passes
+  // after image_rows_done's counter and fence.  A pixel >= M, or a ring wait of
+  // the strip pass that gave up: outputs zero.
   const unsigned ebits = __ldcg(P.err + d.slot);
   const bool bad = ebits != 0u;
   uint64_t* card = P.card + (size_t)d.out * M;
@@ -508,9 +510,23 @@ __device__ void finish_image(const LaunchParams& P, int i, uint64_t* scratch, in
   int32_t* cand = stage_cs ? reinterpret_cast<int32_t*>(dsm + need_cs) : P.cand + (size_t)d.slot * P.cand_stride;
   if (stage_h) {
     unsigned long long* hsm = reinterpret_cast<unsigned long long*>(dsm + at_h);
-    for (int b = threadIdx.x; b < 4 * bins; b += blockDim.x) {
-      hsm[staged_at(b, lb64, [](int i) { return pad_index<kPad64>(i); })] = __ldcg(h + b);
-      h[b] = 0ull;  // clean the workspace slot for the next use
+    // four loads in flight per thread, then the stores (and the slot cleared
+    // for its next use)
+    for (int b0 = threadIdx.x; b0 < 4 * bins; b0 += 4 * blockDim.x) {
+      unsigned long long v4[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u * (int)blockDim.x;
+        v4[u] = b < 4 * bins ? __ldcg(h + b) : 0ull;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u * (int)blockDim.x;
+        if (b < 4 * bins) {
+          hsm[staged_at(b, lb64, [](int i) { return pad_index<kPad64>(i); })] = v4[u];
+          h[b] = 0ull;
+        }
+      }
     }
     __syncthreads();
     curve_epilogue<false, unsigned long long, kPad64>(hsm, hsm + lb64, hsm + 2 * lb64, M, bad, card, sumc, curve, card_s,
@@ -599,7 +615,10 @@ __device__ void image_rows_done(const LaunchParams& P, int i, int64_t n, uint64_
   __syncthreads();
   const bool last = sh_int[0] != 0;
   __syncthreads();
-  if (last) finish_image(P, i, scratch, sh_int, dsm, dsm_bytes);
+  if (last) {
+    __threadfence();  // the other blocks' fenced atomics are read after their counts
+    finish_image(P, i, scratch, sh_int, dsm, dsm_bytes);
+  }
 }
 
 // Image containing global row-strip r: the last image whose first row-strip is
