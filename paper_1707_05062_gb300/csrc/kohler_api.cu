@@ -484,19 +484,17 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   P.bins = bins;
   P.M = M;
   KernelInfo k = kernel_for(route, bins, P.n == 1, t.warps, t.px);
-  // the 4-neighbourhood strip pass leaves the epilogue to k_finish; the
-  // other passes run it in the block that completes an image
-  const bool split = route == Pass::HistU8 || route == Pass::HistU8Check;
+  // the strip passes leave the epilogue to k_finish; the other passes run it
+  // in the block that completes an image
+  const bool split = is_strip(route);
+  const bool n4_strip = route == Pass::HistU8 || route == Pass::HistU8Check;
   const size_t epi = epilogue_smem(M, bins, split ? 0 : k.smem);
   if (!split) k.smem = std::max(k.smem, epi);
   P.smem_bytes = (int32_t)(split ? epi : k.smem);
-  if (split && kohler::take_wait_fault()) P.fail_wait = 1u;
+  if (n4_strip && kohler::take_wait_fault()) P.fail_wait = 1u;
   // pipelined streams: a one-image strip pass takes half the GPU, so that the
   // next call's pass runs beside it and each block's fixed phases (clearing its
   // bins, its first tensor copies, the fold) are spread over twice the rows
-  // (the N8 and N6 strip passes keep the whole GPU: their epilogue runs in
-  // their last block, so the next call cannot start beside them; measured
-  // 45 against 25 us per 18-Mpixel image)
   const int depth = (split && P.n == 1 && kohler::pipelined(stream)) ? 2 : 1;
   const int grid = grid_for(k, rs, t.upw, t.per_sm, depth);
   cudaLaunchConfig_t cfg = {};
@@ -510,7 +508,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
   cudaError_t e;
-  const uint32_t box_w = split ? u8h::kBoxW : u8n::kBoxW;
+  const uint32_t box_w = n4_strip ? u8h::kBoxW : u8n::kBoxW;
   const uint32_t box_h = (uint32_t)u8h::kGroupRows;
   if (is_strip(route) && P.n == 1) {
     // one image: the kernel instance that takes a single tensor map

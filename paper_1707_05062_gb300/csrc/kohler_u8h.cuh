@@ -118,23 +118,38 @@ __device__ __forceinline__ void red_s_hi(uint32_t addr, uint32_t v) {  // the bi
   asm volatile("red.shared.add.u32 [%0+65536], %1;" ::"r"(addr), "r"(v));
 }
 
-// Folds the lane copies of the region into image i's global histograms and
-// (if `clear`) clears the region.  512 threads: thread t owns region row t; it reads the row
-// in 16-byte chunks rotated by t, so that the 8 threads of a quarter warp hit
-// distinct banks.
-__device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uint32_t* region, uint32_t* xch,
-                                               bool clear) {
-  unsigned long long* g = P.hist + (size_t)P.img[i].slot * P.hist_stride;
+// A block's folds of one image happen in two steps.  After every round,
+// u8h_fold_local adds the 32 lane copies of each bin into the thread's totals
+// (thread t owns region row t: the pair sums s = t and, for t < 256, the
+// vertical words of value t, else the right-pair maxima of value t - 256) and
+// clears the lane copies if more updates follow; it reads the row in 16-byte
+// chunks rotated by t, so that the 8 threads of a quarter warp hit distinct
+// banks.  Only at the image's last round of the block (or every
+// kFoldGlobalRounds rounds, which bounds the 32-bit totals) does
+// u8h_fold_global add the totals to the image's global histograms: the one
+// step that writes global memory, and so the one that waits for the previous
+// kernel of the stream.
+struct U8hFoldAcc {
+  uint32_t hs;  // sum bin t
+  uint32_t tm;  // t >= 256: right-pair maxima of value t - 256
+  uint32_t se;  // t < 256: pair ends at value t
+  int32_t sv;   // t < 256: sum of n_lo_v - e_v at value t
+};
+constexpr int kFoldGlobalRounds = 64;
+// a total gets at most 32 lane copies x kNW warps x 8 pixels x rows x 4 (pair
+// ends per pixel) per round
+static_assert((uint64_t)kFoldGlobalRounds * 32 * u8h::kNW * 8 * u8h::kRowsPerRound * 4 < (1ull << 31),
+              "32-bit fold totals");
+
+__device__ __forceinline__ void u8h_fold_local(uint32_t* region, U8hFoldAcc& a, bool clear) {
   const int t = threadIdx.x;
   uint4* const row = reinterpret_cast<uint4*>(region + 64 * t);
-  uint32_t hs = 0, tm = 0, se = 0;
-  int32_t sv = 0;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
     const int cc = (c + t) & 7;
     const uint4 w = row[cc];
     if (clear) row[cc] = make_uint4(0u, 0u, 0u, 0u);
-    hs += w.x + w.y + w.z + w.w;
+    a.hs += w.x + w.y + w.z + w.w;
   }
   if (t < 256) {
 #pragma unroll
@@ -146,8 +161,8 @@ __device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uin
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int32_t lo = (int32_t)(int16_t)(ws[q] & 0xffffu);  // sum of n_lo_v - e_v (signed)
-        sv += lo;
-        se += (ws[q] - (uint32_t)lo) >> 16;                    // sum of pair ends
+        a.sv += lo;
+        a.se += (ws[q] - (uint32_t)lo) >> 16;                    // sum of pair ends
       }
     }
   } else {
@@ -156,18 +171,27 @@ __device__ __forceinline__ void u8h_fold_flush(const LaunchParams& P, int i, uin
       const int cc = 8 + ((c + t) & 7);
       const uint4 w = row[cc];
       if (clear) row[cc] = make_uint4(0u, 0u, 0u, 0u);
-      tm += w.x + w.y + w.z + w.w;
+      a.tm += w.x + w.y + w.z + w.w;
     }
-    xch[t - 256] = tm;
   }
+}
+
+// Adds the totals to image i's global histograms and resets them.  All 512
+// threads; the caller has waited for the previous kernel (wait_prior) and
+// synchronises the block before `xch` is used again.
+__device__ __forceinline__ void u8h_fold_global(const LaunchParams& P, int i, uint32_t* xch, U8hFoldAcc& a) {
+  unsigned long long* g = P.hist + (size_t)P.img[i].slot * P.hist_stride;
+  const int t = threadIdx.x;
+  if (t >= 256) xch[t - 256] = a.tm;
   __syncthreads();
-  if (hs) atomicAdd(g + 512 + t, (unsigned long long)hs);
+  if (a.hs) atomicAdd(g + 512 + t, (unsigned long long)a.hs);
   if (t < 256) {
-    const int64_t hi = (int64_t)xch[t] - (int64_t)sv;  // this block's share of H_hi (may be negative)
-    const int64_t lo = (int64_t)se - hi;
+    const int64_t hi = (int64_t)xch[t] - (int64_t)a.sv;  // this block's share of H_hi (may be negative)
+    const int64_t lo = (int64_t)a.se - hi;
     if (lo) atomicAdd(g + t, (unsigned long long)lo);
     if (hi) atomicAdd(g + 256 + t, (unsigned long long)hi);
   }
+  a = U8hFoldAcc{0u, 0u, 0u, 0};
 }
 
 // The four shared-memory additions of each pixel of one row of 8 pixels (A: bin
@@ -312,6 +336,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
     const int W = d.W, H = d.H;
     uint32_t vmax = 0;
     bool img_failed = false;
+    U8hFoldAcc acc{0u, 0u, 0u, 0};
+    int rounds_acc = 0;
     for (int64_t base = r0; base < seg_end; base += (int64_t)kNW * kRowsPerRound) {
       const int n_r = (int)min64((int64_t)kNW * kRowsPerRound, seg_end - base);
       uint32_t a = (uint32_t)(base - d.rs_begin) + (uint32_t)((n_r * warp) / kNW);
@@ -458,12 +484,16 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         rg.wphase ^= rg.wslot == kSlots - 1 ? 1u : 0u;
         rg.wslot = rg.wslot == kSlots - 1 ? 0u : rg.wslot + 1u;
       }
-      wait_prior();
       __syncthreads();
-      // with SPLIT, the last fold of an image also clears the bins when the
-      // block goes on to another image
-      u8h_fold_flush(P, i, region, xch,
-                     base + (int64_t)kNW * kRowsPerRound < seg_end || (SPLIT && seg_end < r1));
+      // the bins are cleared when more rounds of this image follow, or (SPLIT)
+      // when the block goes on to another image
+      const bool more = base + (int64_t)kNW * kRowsPerRound < seg_end;
+      u8h_fold_local(region, acc, more || (SPLIT && seg_end < r1));
+      if (!more || ++rounds_acc == kFoldGlobalRounds) {
+        wait_prior();
+        u8h_fold_global(P, i, xch, acc);
+        rounds_acc = 0;
+      }
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) {

@@ -38,11 +38,12 @@ constexpr int kRowBytes = 288;                  // left halo, strip, right halo
 constexpr uint32_t kLaneOff = 16;               // the strip's first byte in a ring row
 constexpr uint32_t kBoxW = kRowBytes / 2;       // tensor-copy box: 144 uint16 elements x 4 rows
 constexpr uint32_t kBoxBytes = kRowBytes * u8h::kGroupRows;
-constexpr int kRowsPerRound = 16;               // rows per warp between folds
+constexpr int kRowsPerRound = 28;               // rows per warp between folds
 static_assert(kBoxBytes <= (uint32_t)u8h::kSlotBytes, "ring slot");
 // per pixel the low field adds at most 9 in size, the high field at most 12
 static_assert(u8h::kNW * 8 * kRowsPerRound * 9 < 32768, "signed vertical field overflow");
 static_assert(u8h::kNW * 8 * kRowsPerRound * 12 < 65536, "pair-end field overflow");
+static_assert((uint64_t)kFoldGlobalRounds * 32 * u8h::kNW * 8 * kRowsPerRound * 12 < (1ull << 31), "32-bit fold totals");
 }  // namespace u8n
 
 __device__ __forceinline__ uint32_t flag_lower(uint32_t q, uint32_t p) {  // -1 if q < p (bin addresses)
@@ -150,9 +151,6 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   constexpr int kRowBytesN = u8n::kRowBytes;
   constexpr int kRoundRows = u8n::kRowsPerRound;
   extern __shared__ __align__(16) unsigned char dsm[];
-  __shared__ uint64_t scratch[kScratch];
-  __shared__ int sh_int[kShInts];
-  __shared__ unsigned sh_rows;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(dsm);
   if (sbase + (uint32_t)kLowBytes > kRegion || sbase + (uint32_t)kDynBytes < kRegion + kRegionBytes) {
@@ -173,7 +171,6 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   rg.failed = false;
   if (lane == 0)
     for (int s = 0; s < kSlots; ++s) mbar_init(rg.bar0 + 8u * s, 1u);
-  if (threadIdx.x == 0) sh_rows = 0u;
   {
     uint4* r4 = reinterpret_cast<uint4*>(region);
     for (int k = threadIdx.x; k < (int)(kRegionBytes / 16); k += blockDim.x) r4[k] = make_uint4(0u, 0u, 0u, 0u);
@@ -197,11 +194,12 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
     const int64_t seg_end = min64(r1, d.rs_begin + (int64_t)d.strips * units_col);
     const int W = d.W, H = d.H;
     uint32_t vmax = 0;
+    U8hFoldAcc acc{0u, 0u, 0u, 0};
+    int rounds_acc = 0;
     for (int64_t base = r0; base < seg_end; base += (int64_t)kNW * kRoundRows) {
       const int n_r = (int)min64((int64_t)kNW * kRoundRows, seg_end - base);
       uint32_t a = (uint32_t)(base - d.rs_begin) + (uint32_t)((n_r * warp) / kNW);
       const uint32_t b = (uint32_t)(base - d.rs_begin) + (uint32_t)((n_r * (warp + 1)) / kNW);
-      uint32_t rows_done = 0;
       // producer: as in k_u8h; each box starts 16 bytes left of its strip (the
       // left halo; x stays a multiple of 16 bytes, and the image's first strip
       // reads zeros there)
@@ -243,7 +241,6 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         const int ub = (int)min((uint32_t)units_col, (uint32_t)ua + (b - a));
         a += (uint32_t)(ub - ua);
         const int ya = d.y0 + ua, yb = d.y0 + ub;
-        rows_done += (uint32_t)(yb - ya);
         const int x0 = strip * kStripPx;
         const int xl = x0 + 8 * lane;
         const bool act = xl < W;
@@ -332,10 +329,17 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         }
         while (y < yb) row_any(y++);
       }
-      if (lane == 0 && rows_done) atomicAdd(&sh_rows, rows_done);
-      wait_prior();
       __syncthreads();
-      u8h_fold_flush(P, i, region, xch, base + (int64_t)kNW * kRoundRows < seg_end);
+      // the bins are cleared when more rounds of this image follow or the
+      // block goes on to another image; the image's totals go to global memory
+      // after its last round (as in k_u8h)
+      const bool more = base + (int64_t)kNW * kRoundRows < seg_end;
+      u8h_fold_local(region, acc, more || seg_end < r1);
+      if (!more || ++rounds_acc == kFoldGlobalRounds) {
+        wait_prior();
+        u8h_fold_global(P, i, xch, acc);
+        rounds_acc = 0;
+      }
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
@@ -343,15 +347,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
       atomicOr(P.err + d.slot, kErrInternal);  // the image's outputs become zero, its status KOHLER_ERR_CUDA
       atomicOr(P.sticky, kErrInternal);
     }
-    const unsigned rows = sh_rows;
-    image_rows_done(P, i, rows, scratch, sh_int, reinterpret_cast<unsigned char*>(region), (size_t)kRegionBytes);
-    if (threadIdx.x == 0) sh_rows = 0u;
     r0 = seg_end;
     ++i;
-    if (r0 < r1) {
-      uint4* r4 = reinterpret_cast<uint4*>(region);
-      for (int k = threadIdx.x; k < (int)(kRegionBytes / 16); k += blockDim.x) r4[k] = make_uint4(0u, 0u, 0u, 0u);
-    }
     __syncthreads();
   }
 }
