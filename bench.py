@@ -638,6 +638,31 @@ class _Server:
             raise RuntimeError(f"kohler_poll: {rc}")
         return res.t0, res.count, list(ts)[:self.max_k], res.latency_s
 
+    def submit_many(self, frs):
+        # one call for a batch of pinned frames (kohler_submit_borrowed_many)
+        ct = self.ct
+        arr = (self.K.KohlerFrame * len(frs))()
+        for j, f in enumerate(frs):
+            arr[j] = self.K.KohlerFrame(f.ctypes.data, f.shape[1], f.shape[0], f.strides[0])
+        tickets = (ct.c_uint64 * len(frs))()
+        rc = self.L.kohler_submit_borrowed_many(self.h, arr, len(frs), 1, tickets, None)
+        if rc != 0:
+            raise RuntimeError(f"kohler_submit_borrowed_many: {rc}")
+        return list(tickets)
+
+    def poll_many(self, tickets):
+        ct = self.ct
+        n = len(tickets)
+        bufs = [(ct.c_int32 * max(1, self.max_k))() for _ in range(n)]
+        res = (self.K.KohlerResult * n)()
+        for j in range(n):
+            res[j].thresholds = ct.cast(bufs[j], ct.c_void_p)
+        st = (ct.c_int32 * n)()
+        rc = self.L.kohler_poll_many(self.h, (ct.c_uint64 * n)(*tickets), n, res, st, -1)
+        if rc != 0 or any(st):
+            raise RuntimeError(f"kohler_poll_many: {rc} {list(st)}")
+        return [(res[j].t0, res[j].count, list(bufs[j])[:self.max_k], res[j].latency_s) for j in range(n)]
+
     def stats(self):
         ct = self.ct
         v = [ct.c_uint64() for _ in range(4)]
@@ -652,7 +677,7 @@ def _pct(xs, q):
     return float(np.percentile(np.asarray(xs), q)) if len(xs) else None
 
 
-def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_frames=600, plain_frames=300):
+def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_frames=2000, plain_frames=300):
     """Poisson-arriving video frames of mixed resolutions through the server
     (continuous batching), against one synchronous host call per frame."""
     import queue
@@ -736,9 +761,40 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
                         "by_resolution": {f"{w}x{h}": {"p50_ms": _pct([x[3] for x, (r, _) in zip(results, src) if r == ri], 50) * 1e3,
                                                        "p99_ms": _pct([x[3] for x, (r, _) in zip(results, src) if r == ri], 99) * 1e3}
                                           for ri, (w, h) in enumerate(synth.VIDEO_SIZES)}}
-    # (ii) closed loop: every frame submitted as soon as the staging queue takes it
+    def run_batched(order, B):
+        # closed loop with batched calls: the producer hands over B frames per
+        # kohler_submit_borrowed_many, the consumer collects them with one
+        # kohler_poll_many
+        srv = _Server(K, 256, MAX_K)
+        q = queue.Queue()
+        results = [None] * len(order)
+
+        def producer():
+            for j0 in range(0, len(order), B):
+                js = list(range(j0, min(len(order), j0 + B)))
+                t_sub = time.perf_counter()
+                q.put((js, srv.submit_many([frames[order[j][0]][order[j][1]] for j in js]), t_sub))
+
+        th = threading.Thread(target=producer)
+        t_start = time.perf_counter()
+        th.start()
+        done = 0
+        while done < len(order):
+            js, tickets, t_sub = q.get()
+            res = srv.poll_many(tickets)
+            t_done = time.perf_counter()
+            for j, r in zip(js, res):
+                results[j] = (r[0], r[1], r[2], t_done - t_sub, r[3], t_done - t_sub, 0.0)
+            done += len(js)
+        th.join()
+        t_end = time.perf_counter()
+        stats = srv.stats()
+        srv.close()
+        return results, t_start, t_end, stats
+
+    # (ii) closed loop: batches of 8 frames handed over and collected per call
     sub = src[:closed_frames]
-    results, t_a, t_b, stats = run(sub, None)
+    results, t_a, t_b, stats = run_batched(sub, 8)
     ok = ok and all((r[0], r[1], r[2]) == want[s] for r, s in zip(results, sub))
     lat = [r[3] for r in results]
     out["closed_loop"] = {"frames": len(sub), "fps": len(sub) / (t_b - t_a),
@@ -746,6 +802,7 @@ def form_served(K, torch, dev, n_frames=2000, fps=240.0, distinct=8, closed_fram
                           "latency_ms_p50": _pct(lat, 50) * 1e3, "latency_ms_p99": _pct(lat, 99) * 1e3,
                           "launches": stats[2], "max_frames_per_launch": stats[3],
                           "mean_frames_per_launch": len(sub) / max(1, stats[2]),
+                          "submit": "kohler_submit_borrowed_many, 8 frames per call; kohler_poll_many per batch",
                           "h2d_gb_s": float(sum(frames[r][k].nbytes for r, k in sub)) / (t_b - t_a) / 1e9}
     # (iii) plain: one synchronous host call per frame (pinned frames), in arrival order
     pinned = {key: torch.from_numpy(frames[key[0]][key[1]]) for key in want}

@@ -355,6 +355,23 @@ int kohler_submit(kohler_server* s, const void* host_frame, kohler_dtype dt, int
 int kohler_submit_borrowed(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                            int64_t pitch_bytes, uint64_t* ticket);
 
+/* One host frame of a kohler_submit_borrowed_many call. */
+typedef struct {
+  const void* host_frame; /* pixel (0, 0); caller-owned, see kohler_submit_borrowed */
+  int64_t width;          /* pixels per row */
+  int64_t height;         /* rows */
+  int64_t pitch_bytes;    /* bytes between row starts */
+} kohler_frame;
+
+/* kohler_submit_borrowed for n >= 1 frames of type dt in one call, in order:
+ * tickets[i] identifies frames[i].  Stops at the first frame that fails and
+ * returns its status; *n_submitted (may be NULL) is the number of frames
+ * submitted before it (all n on KOHLER_OK).  The same ownership rule holds for
+ * every frame.  The paper has no counterpart: it saves a call per frame for
+ * producers that hand over several frames at once. */
+int kohler_submit_borrowed_many(kohler_server* s, const kohler_frame* frames, int32_t n, kohler_dtype dt,
+                                uint64_t* tickets, int32_t* n_submitted);
+
 /* kohler_submit that also returns the frame segmented into two classes by its
  * own optimal threshold t0 (Section 4: video frames segmented by the method into
  * two classes, Table 2; classes C_0 = {f <= t0}, C_1 = {f > t0} of Section 2.1,
@@ -374,6 +391,17 @@ int kohler_submit_segment(kohler_server* s, const void* host_frame, kohler_dtype
  * (timeout_us < 0 waits without limit), KOHLER_ERR_RANGE for a frame with a pixel
  * >= M, KOHLER_ERR_ARG for an unknown ticket. */
 int kohler_poll(kohler_server* s, uint64_t ticket, kohler_result* out, int64_t timeout_us);
+
+/* kohler_poll for n >= 1 tickets, in order, with one deadline for the whole
+ * call (timeout_us as in kohler_poll).  status[i] is kohler_poll's result for
+ * tickets[i] and out[i] its result (each out[i].thresholds a caller buffer or
+ * NULL).  Returns KOHLER_OK when every ticket was polled (each status in
+ * status[]), KOHLER_ERR_TIMEOUT (or KOHLER_PENDING for timeout_us = 0) when the
+ * deadline came first: the tickets from the first unfinished one on are not
+ * released and their status[i] is KOHLER_ERR_TIMEOUT (KOHLER_PENDING); they
+ * can be polled again.  KOHLER_ERR_ARG for NULL arrays or n < 1. */
+int kohler_poll_many(kohler_server* s, const uint64_t* tickets, int32_t n, kohler_result* out, int32_t* status,
+                     int64_t timeout_us);
 
 /* Device copy of a finished frame's curve (double[M]) valid until the ticket is
  * polled; NULL pointer if the ticket is unknown or not finished. */

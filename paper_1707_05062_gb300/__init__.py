@@ -50,6 +50,11 @@ class KohlerResult(ctypes.Structure):
                 ("latency_s", ctypes.c_double), ("width", ctypes.c_int64), ("height", ctypes.c_int64)]
 
 
+class KohlerFrame(ctypes.Structure):
+    _fields_ = [("host_frame", ctypes.c_void_p), ("width", ctypes.c_int64), ("height", ctypes.c_int64),
+                ("pitch_bytes", ctypes.c_int64)]
+
+
 def lib():
     """The loaded libkohler (raises if it is missing: no fallback exists)."""
     global _lib
@@ -95,11 +100,14 @@ def lib():
                 L.kohler_submit.argtypes = [p, p, i, i64, i64, i64, p]
                 L.kohler_submit_segment.argtypes = [p, p, i, i64, i64, i64, p, i64, p]
                 L.kohler_submit_borrowed.argtypes = [p, p, i, i64, i64, i64, p]
+                L.kohler_submit_borrowed_many.argtypes = [p, p, i32, i, p, p]
+                L.kohler_poll_many.argtypes = [p, p, i32, p, p, i64]
                 L.kohler_poll.argtypes = [p, ctypes.c_uint64, p, i64]
                 L.kohler_server_curve.argtypes = [p, ctypes.c_uint64, p]
                 L.kohler_server_stats.argtypes = [p, p, p, p, p]
                 L.kohler_server_destroy.argtypes = [p]
-                for name in ("kohler_server_create", "kohler_server_create_ex", "kohler_submit", "kohler_submit_segment", "kohler_submit_borrowed",
+                for name in ("kohler_server_create", "kohler_server_create_ex", "kohler_submit", "kohler_submit_segment",
+                             "kohler_submit_borrowed", "kohler_submit_borrowed_many", "kohler_poll_many",
                              "kohler_poll",
                              "kohler_server_curve",
                              "kohler_server_stats", "kohler_server_destroy"):

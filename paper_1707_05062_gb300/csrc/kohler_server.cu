@@ -577,6 +577,19 @@ int kohler_submit_borrowed(kohler_server* s, const void* host_frame, kohler_dtyp
   return submit_frame(s, host_frame, dt, width, height, pitch_bytes, nullptr, 0, ticket, true);
 }
 
+int kohler_submit_borrowed_many(kohler_server* s, const kohler_frame* frames, int32_t n, kohler_dtype dt,
+                                uint64_t* tickets, int32_t* n_submitted) {
+  if (n_submitted) *n_submitted = 0;
+  if (!s || !frames || !tickets || n < 1) return KOHLER_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    const kohler_frame& f = frames[i];
+    const int rc = submit_frame(s, f.host_frame, dt, f.width, f.height, f.pitch_bytes, nullptr, 0, tickets + i, true);
+    if (rc != KOHLER_OK) return rc;
+    if (n_submitted) *n_submitted = i + 1;
+  }
+  return KOHLER_OK;
+}
+
 int kohler_submit_segment(kohler_server* s, const void* host_frame, kohler_dtype dt, int64_t width, int64_t height,
                           int64_t pitch_bytes, void* host_out, int64_t out_pitch_bytes, uint64_t* ticket) {
   if (!host_out) return KOHLER_ERR_ARG;
@@ -642,6 +655,26 @@ int kohler_poll(kohler_server* s, uint64_t ticket, kohler_result* out, int64_t t
   lk.unlock();
   s->cv_work.notify_one();
   return st;
+}
+
+int kohler_poll_many(kohler_server* s, const uint64_t* tickets, int32_t n, kohler_result* out, int32_t* status,
+                     int64_t timeout_us) {
+  if (!s || !tickets || !out || !status || n < 1) return KOHLER_ERR_ARG;
+  const auto t_end = Clock::now() + std::chrono::microseconds(timeout_us > 0 ? timeout_us : 0);
+  for (int32_t i = 0; i < n; ++i) {
+    int64_t left = timeout_us;
+    if (timeout_us > 0) {
+      left = std::chrono::duration_cast<std::chrono::microseconds>(t_end - Clock::now()).count();
+      if (left < 1) left = 1;  // one more look, then the deadline applies
+    }
+    const int rc = kohler_poll(s, tickets[i], out + i, left);
+    status[i] = rc;
+    if (rc == KOHLER_PENDING || rc == KOHLER_ERR_TIMEOUT) {
+      for (int32_t j = i + 1; j < n; ++j) status[j] = rc;
+      return rc;
+    }
+  }
+  return KOHLER_OK;
 }
 
 int kohler_server_curve(kohler_server* s, uint64_t ticket, const double** dev_curve) {

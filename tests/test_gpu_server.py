@@ -67,6 +67,27 @@ class Server:
         rc = self.L.kohler_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(res), timeout_us)
         return rc, res.t0, res.count, list(ts), res.latency_s
 
+    def submit_many(self, frs):
+        arr = (self.K.KohlerFrame * len(frs))()
+        for j, f in enumerate(frs):
+            arr[j] = self.K.KohlerFrame(f.ctypes.data, f.shape[1], f.shape[0], f.strides[0])
+        tickets = (ctypes.c_uint64 * len(frs))()
+        n_done = ctypes.c_int32(-1)
+        code = 1 if frs[0].dtype == np.uint8 else 2
+        rc = self.L.kohler_submit_borrowed_many(self.h, arr, len(frs), code, tickets, ctypes.byref(n_done))
+        return rc, list(tickets), n_done.value
+
+    def poll_many(self, tickets, timeout_us=-1):
+        n = len(tickets)
+        bufs = [(ctypes.c_int32 * MAX_K)() for _ in range(n)]
+        res = (self.K.KohlerResult * n)()
+        for j in range(n):
+            res[j].thresholds = ctypes.cast(bufs[j], ctypes.c_void_p)
+        st = (ctypes.c_int32 * n)()
+        tk = (ctypes.c_uint64 * n)(*tickets)
+        rc = self.L.kohler_poll_many(self.h, tk, n, res, st, timeout_us)
+        return rc, list(st), [(res[j].t0, res[j].count, list(bufs[j])) for j in range(n)]
+
     def stats(self):
         v = [ctypes.c_uint64() for _ in range(4)]
         assert self.L.kohler_server_stats(self.h, *[ctypes.byref(x) for x in v]) == 0
@@ -286,3 +307,65 @@ def test_segment_submit_arguments(K):
     assert srv.L.kohler_submit_segment(srv.h, f.ctypes.data, 1, 16, 8, 16, None, 16, ctypes.byref(t)) == K.ERR_ARG
     assert srv.L.kohler_submit_segment(srv.h, f.ctypes.data, 1, 16, 8, 16, o.ctypes.data, 8, ctypes.byref(t)) == K.ERR_ARG
     srv.close()
+
+
+def test_submit_and_poll_many(K):
+    # batches of frames handed over and collected in one call each: every result
+    # equals the oracle's, frames share launches, and the calls' edge cases
+    fr = [np.ascontiguousarray(f) for f in frames(40, seed=5)]
+    want = [expected(f) for f in fr]
+    pinned = [torch.from_numpy(f).pin_memory().numpy() for f in fr]
+    s = Server(K)
+    try:
+        for b0 in range(0, len(fr), 8):
+            rc, tickets, n_done = s.submit_many(pinned[b0:b0 + 8])
+            assert rc == 0 and n_done == len(tickets)
+            rc, st, res = s.poll_many(tickets)
+            assert rc == 0 and st == [0] * len(tickets)
+            assert res == want[b0:b0 + len(tickets)]
+        # several batches in flight before the first poll
+        batches = [s.submit_many(pinned[b0:b0 + 10]) for b0 in range(0, 40, 10)]
+        for (rc, tickets, _), b0 in zip(batches, range(0, 40, 10)):
+            assert rc == 0
+            rc, st, res = s.poll_many(tickets)
+            assert rc == 0 and res == want[b0:b0 + 10]
+        assert s.stats()[3] > 1  # frames shared launches
+        # a bad frame stops the batch: the frames before it are submitted
+        bad = pinned[:3] + [np.zeros((0, 0), np.uint8)]
+        arr = (K.KohlerFrame * 4)()
+        for j, f in enumerate(bad[:3]):
+            arr[j] = K.KohlerFrame(f.ctypes.data, f.shape[1], f.shape[0], f.strides[0])
+        arr[3] = K.KohlerFrame(None, 16, 16, 16)
+        tickets = (ctypes.c_uint64 * 4)()
+        n_done = ctypes.c_int32(-1)
+        assert s.L.kohler_submit_borrowed_many(s.h, arr, 4, 1, tickets, ctypes.byref(n_done)) == K.ERR_ARG
+        assert n_done.value == 3
+        rc, st, res = s.poll_many(list(tickets)[:3])
+        assert rc == 0 and res == want[:3]
+        # argument errors
+        assert s.L.kohler_poll_many(s.h, None, 1, None, None, -1) == K.ERR_ARG
+        assert s.L.kohler_submit_borrowed_many(s.h, arr, 0, 1, tickets, None) == K.ERR_ARG
+    finally:
+        s.close()
+
+
+def test_poll_many_deadline_keeps_tickets(K):
+    # a deadline that passes before a batch is done leaves its unfinished
+    # tickets pending; polling them again returns their results
+    big = [np.ascontiguousarray(synth.VideoScene(seed=91).frame(k, 3840, 2160)) for k in range(3)]
+    want = [expected(f) for f in big]
+    s = Server(K, inflight=1)
+    try:
+        rcs = [s.submit(f) for f in big]  # one slot: the frames run one after another
+        assert all(rc == 0 for rc, _ in rcs)
+        tickets = [t for _, t in rcs]
+        rc, st, _ = s.poll_many(tickets, timeout_us=0)
+        assert rc in (K.PENDING, K.ERR_TIMEOUT) or rc == 0
+        if rc != 0:
+            k = st.index(rc)
+            assert all(x == rc for x in st[k:]) and all(x == 0 for x in st[:k])
+            rest = tickets[k:]
+            rc2, st2, res2 = s.poll_many(rest)
+            assert rc2 == 0 and res2 == want[k:]
+    finally:
+        s.close()
