@@ -162,6 +162,70 @@ __device__ __forceinline__ void block_excl_scan_n(uint64_t (&v)[N], uint64_t* sc
   __syncthreads();
 }
 
+// C(t) = sumc / card as the IEEE double nearest to the exact quotient (ties to
+// even), which is what a double division of the two counts gives whenever both
+// are below 2^53 (exactly representable), computed on the integer and FP32
+// pipes instead of GB300's narrow FP64 pipe.  Method: schoolbook long division
+// (Knuth, TAOCP vol. 2, 4.3.1) with both operands normalised to 53 bits,
+// A = a 2^(52 - la), B = b 2^(52 - lb) (la, lb: their top bit positions), so
+// that A / B is in (1/2, 2); then six radix-2^9 digits of A 2^54 / B, each
+// estimated as float(R) * (512 / float(B)) (R < B: relative error below 2^-21,
+// so the estimate is off by at most one) and corrected against the exact
+// 64-bit remainder.  X = floor(A 2^54 / B) then has 54 or 55 bits; its top 53
+// bits are rounded with the next bit and the remaining bits and remainder as
+// sticky.  Counts of 2^53 or more take the double division.
+__device__ __noinline__ double exact_quotient(uint64_t a, uint64_t b) {
+  if (a == 0) return 0.0;
+  if ((a | b) >> 53) return (double)a / (double)b;
+  const int la = 63 - __clzll((long long)a), lb = 63 - __clzll((long long)b);
+  const uint64_t A = a << (52 - la), B = b << (52 - lb);
+  const float rB = 512.0f / __ull2float_rn(B);
+  int e = la - lb;  // unbiased exponent of the result
+  uint64_t X, R;
+  if (A >= B) {
+    X = 1;
+    R = A - B;
+  } else {
+    X = 0;
+    R = A;
+    --e;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    uint32_t d = __float2uint_rz(__fmul_rn(__ull2float_rn(R), rB));
+    int64_t r = (int64_t)(R << 9) - (int64_t)d * (int64_t)B;
+    for (int c = 0; c < 3 && r < 0; ++c) {
+      --d;
+      r += (int64_t)B;
+    }
+    for (int c = 0; c < 3 && r >= (int64_t)B; ++c) {
+      ++d;
+      r -= (int64_t)B;
+    }
+    X = (X << 9) | d;
+    R = (uint64_t)r;
+  }
+  uint64_t m;
+  bool guard, sticky;
+  if (X >> 54) {
+    m = X >> 2;
+    guard = (X >> 1) & 1u;
+    sticky = (X & 1u) || R != 0;
+  } else {
+    m = X >> 1;
+    guard = X & 1u;
+    sticky = R != 0;
+  }
+  if (guard && (sticky || (m & 1u))) {
+    ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++e;
+    }
+  }
+  return __longlong_as_double((long long)((((uint64_t)(e + 1023)) << 52) | (m & ((1ull << 52) - 1))));
+}
+
 // ----------------------------------------------------------------------------- epilogue
 template <bool GLOBAL, class HT>
 __device__ __forceinline__ uint64_t ldh(const HT* p) {
@@ -259,7 +323,7 @@ __device__ void curve_epilogue(const HT* hlo, const HT* hhi, const HT* hs, int M
         card_s[t] = k;
         sumc_s[t] = sm;
       }
-      if (curve) curve[t] = k ? (double)sm / (double)k : 0.0;
+      if (curve) curve[t] = k ? exact_quotient(sm, k) : 0.0;
       rlh += cl + ch;  // RLH(t + 1) = RLH(t) + cumA(t)
     }
   }
