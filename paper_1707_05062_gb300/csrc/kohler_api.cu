@@ -789,6 +789,9 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
   cudaEventCreate(&ev1);
   cudaEventRecord(ev0, caller);
   cudaStreamWaitEvent(stream, ev0, 0);
+  // the tuning runs follow one another on this stream as a caller's
+  // back-to-back launches would (each may overlap the previous one's end)
+  kohler_stream_overlap(stream, 1);
   const int max_k = 16;
   // outputs of the tuning runs, and the reference (default-parameter) histograms
   const size_t cm = (size_t)n * M;
@@ -798,6 +801,7 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
   if (e != cudaSuccess) {
     cudaEventDestroy(ev0);
     cudaEventDestroy(ev1);
+    kohler_stream_overlap(stream, 0);
     cudaStreamDestroy(stream);
     return status_of(e);
   }
@@ -831,8 +835,9 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
                        nullptr, nullptr, nb, &t);
     };
     // One untimed run whose histograms go to `hist`, then `reps` runs captured
-    // in a graph, replayed once untimed and once timed.  Returns the mean time
-    // per launch in microseconds, or a negative value on an error.
+    // in a graph, replayed once untimed and three times timed.  Returns the
+    // mean time per launch of the fastest timed replay in microseconds, or a
+    // negative value on an error.
     auto time_one = [&](const TuneVal& t, std::vector<uint64_t>* hist) -> double {
       if (launch(t)) return -1.0;
       if (cudaMemcpyAsync(hist->data(), card, gm * 8, cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -847,11 +852,16 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
       const cudaError_t ce = cudaStreamEndCapture(stream, &graph);
       double us = -1.0;
       if (r == 0 && ce == cudaSuccess && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-        float ms = 0.f;
-        if (cudaGraphLaunch(exec, stream) == cudaSuccess && cudaEventRecord(ev0, stream) == cudaSuccess &&
-            cudaGraphLaunch(exec, stream) == cudaSuccess && cudaEventRecord(ev1, stream) == cudaSuccess &&
-            cudaEventSynchronize(ev1) == cudaSuccess && cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess)
-          us = 1e3 * (double)ms / reps;
+        bool ok = cudaGraphLaunch(exec, stream) == cudaSuccess;
+        for (int k = 0; k < 3 && ok; ++k) {
+          float ms = 0.f;
+          ok = cudaEventRecord(ev0, stream) == cudaSuccess && cudaGraphLaunch(exec, stream) == cudaSuccess &&
+               cudaEventRecord(ev1, stream) == cudaSuccess && cudaEventSynchronize(ev1) == cudaSuccess &&
+               cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess;
+          const double v = 1e3 * (double)ms / reps;
+          if (ok && (us < 0 || v < us)) us = v;
+        }
+        if (!ok) us = -1.0;
       }
       if (exec) cudaGraphExecDestroy(exec);
       if (graph) cudaGraphDestroy(graph);
@@ -884,7 +894,9 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
         rc = KOHLER_ERR_CUDA;
         break;
       }
-      if (exact && us < best.us) {
+      // another configuration replaces the default only when it is clearly
+      // faster (2 %): closer timings are within the run-to-run spread
+      if (exact && us < best.us && us < 0.98 * def_us) {
         best = t;
         best.us = us;
       }
@@ -903,6 +915,7 @@ int kohler_autotune(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_
   cudaStreamSynchronize(stream);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  kohler_stream_overlap(stream, 0);
   cudaStreamDestroy(stream);
   if (report) {
     const size_t len = std::min(rep.size(), (size_t)report_bytes - 1);
