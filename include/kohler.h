@@ -239,10 +239,11 @@ int kohler_stream_overlap(void* cuda_stream, int32_t mode);
  *     segmentation scratch) fail as if out of memory, without allocating; the
  *     call that needed them returns KOHLER_ERR_NOMEM (a server frame finishes
  *     with it) and leaves no partial state behind.
- *   KOHLER_FAULT_RING_WAIT: in each of the next `count` launches of the uint8
- *     strip pass (4-neighbourhood), one warp treats a completed wait for its
- *     data as failed, exactly as a wait that gave up: the launch's first image
- *     reports KOHLER_ERR_CUDA (out_status, server frame status, and
+ *   KOHLER_FAULT_RING_WAIT: in each of the next `count` launches of a uint8
+ *     strip pass (4-, 8- or 6-neighbourhood), one warp of the first block
+ *     treats a completed wait for its data as failed, exactly as a wait that
+ *     gave up: the launch's first image (and any later image that block works
+ *     on) reports KOHLER_ERR_CUDA (out_status, server frame status, and
  *     kohler_stream_status) and its outputs are zero.
  * count = 0 cancels.  KOHLER_ERR_ARG for another kind or count < 0. */
 enum { KOHLER_FAULT_ALLOC = 1, KOHLER_FAULT_RING_WAIT = 2 };

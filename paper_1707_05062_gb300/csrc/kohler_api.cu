@@ -491,7 +491,7 @@ int launch_group(Pass pass, const std::vector<int>& idx, const kohler_image* img
   const size_t epi = epilogue_smem(M, bins, split ? 0 : k.smem);
   if (!split) k.smem = std::max(k.smem, epi);
   P.smem_bytes = (int32_t)(split ? epi : k.smem);
-  if (n4_strip && kohler::take_wait_fault()) P.fail_wait = 1u;
+  if (split && kohler::take_wait_fault()) P.fail_wait = 1u;
   // pipelined streams: a one-image strip pass takes half the GPU, so that the
   // next call's pass runs beside it and each block's fixed phases (clearing its
   // bins, its first tensor copies, the fold) are spread over twice the rows

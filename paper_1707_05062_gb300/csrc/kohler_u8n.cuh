@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
   rg.cur = 0u;
   rg.rin = 0;
   rg.failed = false;
+  uint32_t issued = 0, waited = 0;  // copies of this warp issued and waited for
+  const bool inject = P.fail_wait != 0u && blockIdx.x == 0 && warp == 0;
   if (lane == 0)
     for (int s = 0; s < kSlots; ++s) mbar_init(rg.bar0 + 8u * s, 1u);
   {
@@ -220,18 +222,29 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         }
         const uint32_t slot = rg.islot;
         rg.islot = slot == kSlots - 1 ? 0u : slot + 1u;
-        if (lane == 0) {
-          const uint32_t bar = rg.bar0 + 8u * slot;
-          fence_proxy_async();
-          mbar_expect_tx(bar, u8n::kBoxBytes);
-          tma_2d(rg.ring0 + slot * kSlotBytes, map, (p_x0 >> 1) - 8, p_y0 + p_gi * kGroupRows, bar);
+        if (!rg.failed) {  // after a failed wait no further copy is issued
+          if (lane == 0) {
+            const uint32_t bar = rg.bar0 + 8u * slot;
+            fence_proxy_async();
+            mbar_expect_tx(bar, u8n::kBoxBytes);
+            tma_2d(rg.ring0 + slot * kSlotBytes, map, (p_x0 >> 1) - 8, p_y0 + p_gi * kGroupRows, bar);
+          }
+          ++issued;
         }
         ++p_gi;
       };
       for (int k = 0; k < kSlots; ++k) produce();
+      // as in k_u8h: a wait that gives up (or the injected failure of the
+      // first wait, which has completed) marks the warp failed; its later
+      // waits return at once and the copies in flight are waited for below
       auto wait_group = [&]() {
-        if (!mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase)) rg.failed = true;
         rg.cur = rg.ring0 + rg.wslot * kSlotBytes + u8n::kLaneOff + 8u * (uint32_t)lane;
+        if (rg.failed) return;
+        if (!mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase) || (inject && waited == 0)) {
+          rg.failed = true;
+          if (!inject || waited != 0) return;
+        }
+        ++waited;
         rg.wphase ^= rg.wslot == kSlots - 1 ? 1u : 0u;
         rg.wslot = rg.wslot == kSlots - 1 ? 0u : rg.wslot + 1u;
       };
@@ -329,6 +342,14 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
         }
         while (y < yb) row_any(y++);
       }
+      // copies in flight after a failed wait: wait for them (bounded) before
+      // the ring's memory is reused or the block exits
+      while (rg.failed && waited < issued) {
+        mbar_wait(rg.bar0 + 8u * rg.wslot, rg.wphase);
+        ++waited;
+        rg.wphase ^= rg.wslot == kSlots - 1 ? 1u : 0u;
+        rg.wslot = rg.wslot == kSlots - 1 ? 0u : rg.wslot + 1u;
+      }
       __syncthreads();
       // the bins are cleared when more rounds of this image follow or the
       // block goes on to another image; the image's totals go to global memory
@@ -343,7 +364,7 @@ __global__ void __launch_bounds__(u8h::kNW * 32, 1)
       __syncthreads();
     }
     if (CHECK && vmax > vlimit) atomicOr(P.err + d.slot, kErrRange);
-    if (rg.failed) {
+    if (rg.failed && lane == 0) {
       atomicOr(P.err + d.slot, kErrInternal);  // the image's outputs become zero, its status KOHLER_ERR_CUDA
       atomicOr(P.sticky, kErrInternal);
     }

@@ -134,8 +134,12 @@ def test_injected_allocation_failures(K):
     img_np = synth.smooth_image(41, 320, 200, 256)
     img = torch.from_numpy(img_np).cuda()
     want = want_of(img_np)
-    # a stream without a workspace yet: the first call allocates it
+    # a stream without a workspace: torch hands out pooled stream handles, which
+    # an earlier test may have used, so every workspace is released first and
+    # the next call on the stream allocates one
     s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    assert K.lib().kohler_release() == 0
     K.test_inject(K.FAULT_ALLOC, 1)
     with pytest.raises(K.KohlerError) as e:
         K.analyze_batch([img], 256, MAX_K, stream=s)
@@ -151,9 +155,11 @@ def test_injected_allocation_failures(K):
     assert e.value.status == K.ERR_NOMEM
     card, sumc, c, ts, cnt, t0 = K.analyze_host(img_np, 256, MAX_K)
     assert np.array_equal(card, want[0]) and np.array_equal(sumc, want[1]) and int(t0) == want[5]
-    # segmentation scratch of a new stream
+    # segmentation scratch of a stream (released first: pooled handles)
     s2 = torch.cuda.Stream()
     out = torch.empty_like(img)
+    torch.cuda.synchronize()
+    assert K.lib().kohler_release() == 0
     res = K.analyze_batch([img], 256, 6, stream=s2)
     K.test_inject(K.FAULT_ALLOC, 1)
     with pytest.raises(K.KohlerError) as e:
@@ -193,9 +199,28 @@ def test_injected_allocation_failures(K):
                                         *[o.data_ptr() for o in outs], ctypes.c_void_p(s3.cuda_stream))
     s3.synchronize()
     assert rc == 0 and int(outs[6].item()) == 0 and same(outs[:6], want)
+    assert K.lib().kohler_release() == 0  # the next call allocates a workspace
     with pytest.raises(K.KohlerError):  # the injection was still pending
         K.analyze_batch([img], 256, MAX_K, stream=torch.cuda.Stream())
     K.test_inject(K.FAULT_ALLOC, 0)
+
+
+@pytest.mark.parametrize("nb", [8, 6])
+def test_ring_wait_failure_other_neighbourhoods(K, nb):
+    # the N8 / N6 strip pass takes the same failure path as the N4 one
+    img_np = synth.smooth_image(43, 1024, 300, 256)
+    img = torch.from_numpy(img_np).cuda()
+    want = want_of(img_np, nb=nb)
+    s = torch.cuda.Stream()
+    got = K.analyze_batch([img], 256, MAX_K, stream=s, nbhd=nb)
+    torch.cuda.synchronize()
+    assert K.stream_status(s) == K.OK and same(got, want)
+    K.test_inject(K.FAULT_RING_WAIT, 1)
+    got = K.analyze_batch([img], 256, MAX_K, stream=s, nbhd=nb)
+    assert K.stream_status(s) == K.ERR_CUDA
+    assert not got[0].any() and not got[1].any() and not got[2].any()
+    got = K.analyze_batch([img], 256, MAX_K, stream=s, nbhd=nb)
+    assert K.stream_status(s) == K.OK and same(got, want)
 
 
 def test_ring_wait_failure_reports_cuda_error(K):
