@@ -200,10 +200,11 @@ __device__ __forceinline__ void seg_walk(const SegParams& p, Chunk chunk, Elem e
 // into one of kSegCopies global copies (fewer blocks add into the same word).
 // The last block adds the copies up and builds the class table.
 //
-// Launched after another kernel of this library it may start early: it only
-// reads the image before griddepcontrol.wait (the library's kernels never write
-// images that a later call reads, except k_seg_map, which does not let its
-// successor start early), and it waits before its first global write.
+// On a stream that allows the overlap (kohler_stream_overlap) it may start
+// before the previous kernel ends: it only reads the image before
+// griddepcontrol.wait (the library's kernels never write images that a later
+// call reads, except k_seg_map, which does not let its successor start early),
+// and it waits before its first global write.
 template <int ELEM, bool CHECK>
 __global__ void __launch_bounds__(kSegThreads) k_seg_hist(const SegParams p) {
   extern __shared__ __align__(16) uint32_t sh_bins[];  // the bins, then the table block's scratch
@@ -498,7 +499,10 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
     }
   }
   void* args[] = {&p};
-  // programmatic dependent launch for both (see the kernels for what each waits for)
+  // programmatic dependent launch (see the kernels for what each waits for):
+  // the counting pass only when the caller allowed the overlap on its stream
+  // (it reads the image before it waits), the mapping pass always (it waits
+  // for the counting pass before anything else)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid_h);
   cfg.blockDim = dim3(kSegThreads);
@@ -507,9 +511,10 @@ extern "C" int kohler_segment(const void* img, kohler_dtype dt, int64_t width, i
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = kohler::overlap_allowed(stream) ? 1 : 0;
   cfg.dynamicSmemBytes = smem_h;
   cudaError_t e = cudaLaunchKernelExC(&cfg, fh, args);
+  cfg.numAttrs = 1;
   cfg.dynamicSmemBytes = smem_m;
   cfg.gridDim = dim3(grid_m);
   if (e == cudaSuccess) e = cudaLaunchKernelExC(&cfg, fm, args);
