@@ -117,9 +117,10 @@ int kohler_curve_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int
 int kohler_thresholds(const uint64_t* card, const uint64_t* sumc, int32_t n, int32_t M, int32_t max_k,
                       int32_t* out_t, int32_t* out_count, int32_t* out_t0, void* cuda_stream);
 
-/* kohler_curve_batch followed by kohler_thresholds, fused: the last block to
- * finish an image computes its curve and thresholds in the same launch.
- * Outputs as in the two calls above (curve may be NULL). */
+/* kohler_curve_batch followed by kohler_thresholds, fused: each image's curve
+ * and thresholds come from its histograms right after its pass, by a block of
+ * one kernel launched behind the uint8 strip passes, else by the pass's last
+ * block for the image.  Outputs as in the two calls above (curve may be NULL). */
 int kohler_analyze_batch(const kohler_image* imgs, int32_t n, kohler_dtype dt, int32_t M, kohler_nbhd nb,
                          int32_t max_k, uint64_t* card, uint64_t* sumc, double* curve, int32_t* out_t,
                          int32_t* out_count, int32_t* out_t0, void* cuda_stream);
