@@ -221,7 +221,45 @@ def cpu_baseline(img: np.ndarray, M: int, budget_s: float = 12.0):
     return {"value": px / elapsed / 1e9, "unit": UNIT, "cores": int(os.environ.get("OMP_NUM_THREADS", cores)),
             "kind": "oracle",
             "sample": f"rows 0..{rows - 1} of the {img.shape[1]}x{img.shape[0]} image ({band.size / 1e6:.2f} Mpixel), "
-                      f"{reps} run(s), {elapsed:.1f} s: per-threshold loop over N4* pairs + normalisation + thresholds"}
+                      f"{reps} run(s), {elapsed:.1f} s: per-threshold loop over N4* pairs + normalisation + thresholds",
+            "single_thread": cpu_single_thread(M)}
+
+
+_SINGLE = r'''
+import json, sys, time
+sys.path.insert(0, ROOT)
+import numpy as np, oracle, synth
+oracle.build()
+out = {}
+for name, img in (("blobs_256", synth.blobs_image()), ("voronoi_18mp_rows_0_47", synth.voronoi_18mp()[:48])):
+    img = np.ascontiguousarray(img)
+    n, t = 0, time.perf_counter()
+    while n == 0 or time.perf_counter() - t < 1.5:
+        card, sumc = oracle.curve(img, M)
+        oracle.normalise(card, sumc)
+        oracle.thresholds(card, sumc, MAX_K)
+        n += 1
+    dt = (time.perf_counter() - t) / n
+    out[name] = {"ms_per_image": dt * 1e3, "gpx_s": img.size / dt / 1e9, "runs": n}
+print(json.dumps(out))
+'''
+
+
+def cpu_single_thread(M: int):
+    """The oracle on one host thread (a fresh process with OMP_NUM_THREADS=1),
+    on the 256x256 image and a 48-row band of the 18-Mpixel image, as the paper's
+    single-thread rows are timed."""
+    import subprocess
+
+    code = _SINGLE.replace("ROOT", repr(ROOT)).replace("MAX_K", str(MAX_K)).replace("M)", f"{M})")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+        res = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal
+        return {"error": repr(e)[:200]}
+    res["cores"] = 1
+    return res
 
 
 # ----------------------------------------------------------------------------- workloads
