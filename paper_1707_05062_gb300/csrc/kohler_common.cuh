@@ -168,18 +168,24 @@ __device__ __forceinline__ void block_excl_scan_n(uint64_t (&v)[N], uint64_t* sc
 // pipes instead of GB300's narrow FP64 pipe.  Method: schoolbook long division
 // (Knuth, TAOCP vol. 2, 4.3.1) with both operands normalised to 53 bits,
 // A = a 2^(52 - la), B = b 2^(52 - lb) (la, lb: their top bit positions), so
-// that A / B is in (1/2, 2); then six radix-2^9 digits of A 2^54 / B, each
-// estimated as float(R) * (512 / float(B)) (R < B: relative error below 2^-21,
-// so the estimate is off by at most one) and corrected against the exact
-// 64-bit remainder.  X = floor(A 2^54 / B) then has 54 or 55 bits; its top 53
-// bits are rounded with the next bit and the remaining bits and remainder as
-// sticky.  Counts of 2^53 or more take the double division.
+// that A / B is in (1/2, 2); then six radix-2^9 digits of A 2^54 / B.  Each
+// digit is estimated from the top 23 bits of the remainder R and of B in
+// float32, float(R >> 30) * (512 / float(B >> 30)) rounded to an integer
+// (both conversions exact: 2^23 + v read as a float is exact for v < 2^23, so
+// no conversion instruction is used; the estimate is off by at most two), and
+// corrected against the exact 64-bit remainder.  X = floor(A 2^54 / B) then has
+// 54 or 55 bits; its top 53 bits are rounded with the next bit and the
+// remaining bits and remainder as sticky.  Counts of 2^53 or more take the
+// double division.
+__device__ __forceinline__ float exact_f23(uint32_t v) {  // v < 2^23
+  return __fsub_rn(__int_as_float(0x4B000000 | v), 8388608.0f);
+}
 __device__ __noinline__ double exact_quotient(uint64_t a, uint64_t b) {
   if (a == 0) return 0.0;
   if ((a | b) >> 53) return (double)a / (double)b;
   const int la = 63 - __clzll((long long)a), lb = 63 - __clzll((long long)b);
   const uint64_t A = a << (52 - la), B = b << (52 - lb);
-  const float rB = 512.0f / __ull2float_rn(B);
+  const float rB = __fdiv_rn(512.0f, exact_f23((uint32_t)(B >> 30)));
   int e = la - lb;  // unbiased exponent of the result
   uint64_t X, R;
   if (A >= B) {
@@ -192,8 +198,11 @@ __device__ __noinline__ double exact_quotient(uint64_t a, uint64_t b) {
   }
 #pragma unroll
   for (int k = 0; k < 6; ++k) {
-    uint32_t d = __float2uint_rz(__fmul_rn(__ull2float_rn(R), rB));
-    int64_t r = (int64_t)(R << 9) - (int64_t)d * (int64_t)B;
+    // the estimate rounded to the nearest integer: x + 2^23 keeps it in the
+    // float's low mantissa bits (x < 2^22)
+    const float x = __fadd_rn(__fmul_rn(exact_f23((uint32_t)(R >> 30)), rB), 8388608.0f);
+    uint32_t d = __float_as_uint(x) & 0x7FFFFFu;
+    int64_t r = (int64_t)(R << 9) - (int64_t)((uint64_t)d * B);
     for (int c = 0; c < 3 && r < 0; ++c) {
       --d;
       r += (int64_t)B;

@@ -141,7 +141,14 @@ def test_autotune_u16_and_u8_batch():
     for g in rep["groups"]:
         assert g["candidates"] and all(c["exact"] for c in g["candidates"])
         assert g["best"]["us"] <= g["default_us"] + 1e-9
-        assert g["best"]["us"] == min([g["default_us"]] + [c["us"] for c in g["candidates"]])
+        # the default stays unless a configuration is at least 2 % faster; then
+        # the fastest one is kept
+        # (the report rounds to 1 ns: at the 2 % boundary either is right)
+        fastest = min(c["us"] for c in g["candidates"])
+        if abs(fastest - 0.98 * g["default_us"]) < 0.002:
+            assert g["best"]["us"] in (fastest, g["default_us"])
+        else:
+            assert g["best"]["us"] == (fastest if fastest < 0.98 * g["default_us"] else g["default_us"])
     assert k.tune_count() == 2
     check(imgs, 256, tag="after tuning")
     rep16 = k.autotune([dev(im) for im in U16], 4096, reps=3)

@@ -4,8 +4,9 @@ Python's correctly rounded division on CPU.
 
 The device computes the quotient of two counts below 2^53 without the FP64
 pipe: both operands normalised to 53 bits, six radix-2^9 long-division digits
-estimated in float32 and corrected against the exact remainder, then rounding
-to nearest even on the top 53 bits.  The GPU parity tests compare every C(t)
+estimated in float32 from the top 23 bits of the remainder and of the divisor
+and corrected against the exact remainder, then rounding to nearest even on
+the top 53 bits.  The GPU parity tests compare every C(t)
 with the oracle's double division bit for bit; this test shows that the method
 itself is exact (the digit estimate is never off by more than the correction
 allows), over structured and random operands, including the ranges the curve
@@ -19,19 +20,27 @@ import numpy as np
 F = np.float32
 
 
+def f23(v: int) -> np.float32:
+    """float32 of v < 2^23, as the device makes it: 2^23 + v read as a float, less 2^23."""
+    assert 0 <= v < (1 << 23)
+    x = np.frombuffer(struct.pack("<I", 0x4B000000 | v), dtype=np.float32)[0]
+    return F(x - F(8388608.0))
+
+
 def quotient(a: int, b: int) -> float:
     if a == 0:
         return 0.0
     la, lb = a.bit_length() - 1, b.bit_length() - 1
     A, B = a << (52 - la), b << (52 - lb)
-    rB = F(512.0) / F(B)  # float32 division, round to nearest
+    rB = F(512.0) / f23(B >> 30)  # float32 division, round to nearest
     if A >= B:
         X, R, e = 1, A - B, la - lb
     else:
         X, R, e = 0, A, la - lb - 1
     worst = 0
     for _ in range(6):
-        d = int(F(R) * rB)  # float32 product, truncated
+        x = F(F(f23(R >> 30) * rB) + F(8388608.0))  # float32 product, then rounded to an integer
+        d = struct.unpack("<I", struct.pack("<f", x))[0] & 0x7FFFFF
         r = (R << 9) - d * B
         fix = 0
         while r < 0:
